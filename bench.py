@@ -1,0 +1,461 @@
+"""Benchmark of the GB / C(pH,E)MD / E-REMD hot path on one GB300.
+
+Workload: E-REMD batch of 8 replicas x 2048-atom compact chains (1 redox + 3 pH
+sites), E ladder E0 +- 0.2 V, Langevin 2 fs with GB + Coulomb + chain bonds +
+soft repulsion, MC attempt (protonation then redox) every 10 steps, neighbour
+exchange every 100 steps.  One bench "step" = one exchange period: 100 MD
+steps of every replica, 10 MC rounds, 1 exchange, run through gb_md_segment
+(one CUDA graph replay).
+
+Headline metric: GB pair-interactions/s = sum_r N_r (N_r - 1)/2 per MD step
+x MD steps / device seconds (each MD step evaluates all pairs in three passes).
+Also reported: replica MD-steps/s, the plain form (one context and one launch
+sequence per replica, no graph), the dominant pass's FP32 roofline, an
+end-to-end number through host buffers, and the FP64 oracle on host cores.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this build).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+MD_PER_STEP = 100          # MD steps per bench step (one exchange period)
+MC_EVERY, EX_EVERY = 10, 100
+N_REP, N_ATOMS = 8, 2048
+SM_COUNT = 152
+FP32_LANES = 128           # FP32 lanes per SM
+# algorithmic FP32 flops per unordered pair (FMA = 2), per pass; see the design doc
+FLOPS_PER_PAIR = {"born": 57, "energy": 47, "chain": 80}
+MUFU_PER_PAIR = {"born": 1, "energy": 3, "chain": 1}
+PASS_NAMES = ["born", "energy", "chain"]
+
+
+def workload():
+    import synth
+    return synth.config_eremd(N_REP, N_ATOMS, seed=0)
+
+
+# ----------------------------------------------------------------------------------
+# clocks during the timed region
+class ClockSampler:
+    def __init__(self, gpu_index=0):
+        self.samples = []
+        self.proc = None
+        self.gpu = gpu_index
+        self.thread = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for s in self.samples for n, v in zip(names, s[5:9]) if v.strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ----------------------------------------------------------------------------------
+def reference_arm(args):
+    """The FP64 oracle on host cores, on a bounded sample of the same workload:
+    each step = 2 MD steps of one 2048-atom replica (the 8 replicas are
+    identical and independent between exchanges)."""
+    import oracle
+    oracle.build()
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    b = workload()
+    one = b.replicas[0]
+    import synth
+    sb = synth.Batch([one], pH=b.pH[:1], E=b.E[:1])
+    x, q, rho, scr, off = oracle.batch_arrays(sb)
+    v = np.zeros_like(x)
+    p = oracle.default_params()
+    F, _ = oracle.forces_all(off, x, q, rho, scr, p)
+    md_per = 2
+    for w in range(args.warmup):
+        for k in range(md_per):
+            oracle.md_step(off, x, v, q, rho, scr, F, 1, w * md_per + k + 1, p)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        for k in range(md_per):
+            oracle.md_step(off, x, v, q, rho, scr, F, 1, 10_000 + s * md_per + k, p)
+    dt = time.perf_counter() - t0
+    pairs = one.n * (one.n - 1) // 2
+    value = pairs * md_per * args.steps / dt
+    line = {
+        "impl": "reference", "metric": "GB pair-interactions/s", "value": value,
+        "unit": "pair-interactions/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"eremd_{N_REP}x{N_ATOMS}", "sample": "1 replica x 2 MD steps per step"},
+        "cpu_baseline": {"value": value, "unit": "pair-interactions/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} x 2 MD steps of one {one.n}-atom replica"},
+        "e2e": {"value": value, "unit": "pair-interactions/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(seconds=12.0):
+    """FP64 oracle force evaluation + BAOAB step of one 2048-atom replica,
+    repeated for about `seconds` of single-core CPU time."""
+    import oracle
+    import synth
+    oracle.build()
+    b = workload()
+    one = b.replicas[0]
+    sb = synth.Batch([one], pH=b.pH[:1], E=b.E[:1])
+    x, q, rho, scr, off = oracle.batch_arrays(sb)
+    v = np.zeros_like(x)
+    p = oracle.default_params()
+    F, _ = oracle.forces_all(off, x, q, rho, scr, p)
+    n_steps = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds or n_steps < 3:
+        oracle.md_step(off, x, v, q, rho, scr, F, 1, n_steps + 1, p)
+        n_steps += 1
+    dt = time.perf_counter() - t0
+    pairs = one.n * (one.n - 1) // 2
+    return {"value": pairs * n_steps / dt, "unit": "pair-interactions/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n_steps} BAOAB MD steps (GB+Coulomb+restraint forces) of one {one.n}-atom replica, "
+                      f"{dt:.1f} s single-threaded"}
+
+
+# ----------------------------------------------------------------------------------
+class Setup:
+    """Device state of the workload and the gb_md_state that points at it."""
+
+    def __init__(self, pkg, batch, dev, seed, params):
+        import torch
+        self.pkg, self.b, self.dev = pkg, batch, dev
+        self.ctx = pkg.Context(batch.atom_off, params)
+        N, M = batch.n_atoms, batch.n_rep
+        self.xyzq = torch.as_tensor(batch.xyzq(), device=dev)
+        self.rad = torch.as_tensor(batch.rad_screen(), device=dev)
+        self.vel = torch.zeros((N, 4), dtype=torch.float32, device=dev)
+        self.force = torch.zeros((N, 4), dtype=torch.float32, device=dev)
+        self.R = torch.zeros(N, dtype=torch.float32, device=dev)
+        G = site_reference_energies_gpu(pkg, batch, dev, params)
+        self.tables = batch.site_tables(G)
+        self.sites = pkg.SiteTables(self.tables, M, dev)
+        self.state = torch.zeros(self.tables["n_sites"], dtype=torch.int32, device=dev)
+        self.pH = torch.as_tensor(batch.pH.copy(), device=dev)
+        self.E = torch.as_tensor(batch.E.copy(), device=dev)
+        lad = batch.E_ladder if batch.E_ladder is not None else batch.E[:1]
+        self.E_ladder = torch.as_tensor(np.asarray(lad, np.float64), device=dev)
+        self.pH_ladder = torch.as_tensor(np.asarray([batch.pH[0]], np.float64), device=dev)
+        self.grid = torch.arange(M, dtype=torch.int32, device=dev)
+        st = pkg.MDState()
+        st.xyzq, st.vel, st.force = self.xyzq.data_ptr(), self.vel.data_ptr(), self.force.data_ptr()
+        st.rad_screen, st.R = self.rad.data_ptr(), self.R.data_ptr()
+        st.state, st.pH, st.E = self.state.data_ptr(), self.pH.data_ptr(), self.E.data_ptr()
+        st.grid, st.E_ladder, st.pH_ladder = (self.grid.data_ptr(), self.E_ladder.data_ptr(),
+                                              self.pH_ladder.data_ptr())
+        st.n_E, st.n_pH = M, 1
+        st.dt, st.friction, st.mass, st.kT = 0.002, 10.0, 12.0, pkg.KB * 300.0
+        st.bond_k, st.bond_r0 = 300.0, 1.5
+        st.seed, st.step, st.attempt = seed, 0, 0
+        st.mc_every, st.ex_every, st.ex_dim, st.wrap = MC_EVERY, EX_EVERY, 0, 1
+        self.st = st
+        self.ctx.md_init(st)
+
+
+def site_reference_energies_gpu(pkg, batch, dev, params):
+    """G_ref(s) = E_elec(q(s)) - E_elec(q(0)) at the starting conformation, from
+    gb_energy_forces (GB + Coulomb, repulsion excluded) on the device."""
+    import torch
+    t = batch.site_tables()
+    G = np.zeros(t["site_state_off"][-1])
+    p0 = pkg.default_params(alpha=params.alpha, beta=params.beta, gamma=params.gamma,
+                            offset=params.offset, eps_in=params.eps_in, eps_out=params.eps_out)
+    cache = {}
+    for r, rep in enumerate(batch.replicas):
+        key = id(rep)
+        if key in cache:
+            lo = t["site_off"][r]
+            G[t["site_state_off"][lo]:t["site_state_off"][t["site_off"][r + 1]]] = cache[key]
+            continue
+        ctx = pkg.Context([0, rep.n], p0)
+        base = np.zeros((rep.n, 4), np.float32)
+        base[:, :3], base[:, 3] = rep.xyz, rep.q
+        rad = torch.as_tensor(np.stack([rep.rho, rep.screen], 1).astype(np.float32), device=dev)
+
+        def elec(qv):
+            x = base.copy()
+            x[:, 3] = qv
+            E = ctx.energy_forces(torch.as_tensor(x, device=dev), rad, want=("E",))["E"]
+            return float(E[0, 0] + E[0, 1])
+
+        e0 = elec(rep.q)
+        vals = []
+        for s in rep.sites:
+            for k in range(s.n_states):
+                qq = rep.q.copy()
+                qq[s.atoms] = s.q_state[k]
+                vals.append(elec(qq) - e0)
+        lo = t["site_off"][r]
+        G[t["site_state_off"][lo]:t["site_state_off"][t["site_off"][r + 1]]] = vals
+        cache[key] = vals
+        ctx.close()
+    return G
+
+
+def launches_per_segment(md_steps):
+    """Kernels of this library enqueued by one gb_md_segment call of md_steps."""
+    per_md = 7                                     # first half, 3 pair passes, 2 finalizers, second half
+    mc = 2 * (md_steps // MC_EVERY)                # protonation + redox attempt kernels
+    ex = 2 * (md_steps // EX_EVERY)                # exchange + attempt counter
+    return 1 + per_md * md_steps + mc + ex + 1     # + set counters, + advance step counter
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=150)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--autotune", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        torch.distributed.barrier()
+    import paper_1803_09652_gb300 as pkg
+    pkg.load()
+
+    params = pkg.default_params(rep_k=10.0, rep_sigma=2.5)
+    b = workload()
+    S = Setup(pkg, b, dev, seed=1234 + rank, params=params)
+    if args.autotune:
+        S.ctx.autotune(S.xyzq, S.rad)
+    S.ctx.set_profiling(True)
+    stream = torch.cuda.current_stream()
+    pairs_md = b.pairs_per_eval()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+
+    for _ in range(args.warmup):
+        S.ctx.md_segment(S.st, S.sites, MD_PER_STEP)
+    torch.cuda.synchronize()
+    S.ctx.sync_status()
+
+    # ---- timed region: K bench steps, L2 flushed between steps ------------------
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    pass_ms = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        S.ctx.md_segment(S.st, S.sites, MD_PER_STEP)
+        ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        pass_ms.append(S.ctx.pass_times())
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    S.ctx.sync_status()
+    step_ms = [a.elapsed_time(c) for a, c in ev]
+    dev_s = sum(step_ms) / 1000.0
+    if world > 1:
+        t = torch.tensor([dev_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        dev_s = float(t.item())
+    total_pairs = pairs_md * MD_PER_STEP * args.steps * world
+    value = total_pairs / dev_s
+    rep_steps = b.n_rep * MD_PER_STEP * args.steps * world / dev_s
+    pm = np.mean(np.array(pass_ms), axis=0)
+
+    # ---- roofline of the dominant pass (FP32 ALU bound) --------------------------
+    dom = int(np.argmax(pm))
+    name = PASS_NAMES[dom]
+    achieved = pairs_md * FLOPS_PER_PAIR[name] / (pm[dom] * 1e-3) / 1e12
+    sm_max = (clk.get("sm_max_mhz") or 2070.0)
+    peak = SM_COUNT * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    sm_load = clk.get("sm_mhz") or sm_max
+    peak_load = SM_COUNT * FP32_LANES * 2 * sm_load * 1e6 / 1e12
+    all_flops = pairs_md * sum(FLOPS_PER_PAIR.values())
+    step_fp32 = all_flops * MD_PER_STEP * args.steps / dev_s / 1e12
+    traffic = read_traffic(name)
+
+    # ---- plain form: one context per replica, direct launches, no graph ---------
+    plain = None
+    if not args.no_plain and rank == 0:
+        plain = plain_form(pkg, b, dev, params, n_bench=max(1, min(3, args.steps)))
+
+    # ---- end to end through host buffers ----------------------------------------
+    e2e = end_to_end(pkg, S, dev, n_bench=max(2, min(5, args.steps)), pairs_md=pairs_md)
+
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        cpu = cpu_baseline()
+
+    if rank == 0:
+        line = {
+            "metric": "GB pair-interactions/s", "value": value, "unit": "pair-interactions/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * dev_s / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 pairs, int64 fixed-point sums, f64 totals",
+            "data": "synthetic",
+            "config": {"workload": f"eremd_{N_REP}x{N_ATOMS}", "replicas": b.n_rep,
+                       "atoms_per_replica": N_ATOMS, "md_steps_per_step": MD_PER_STEP,
+                       "mc_every": MC_EVERY, "exchange_every": EX_EVERY,
+                       "pairs_per_md_step": pairs_md, "l2": "flushed between steps (256 MB write)",
+                       "tiles": list(S.ctx.tiles()), "parallelism": "replicas batched on one GPU"},
+            "replica_md_steps_per_s": rep_steps,
+            "pass_ms": dict(zip(PASS_NAMES, [float(v) for v in pm])),
+            "fp32_flops_per_pair": FLOPS_PER_PAIR,
+            "fp32_tflops_whole_step": step_fp32,
+            "fp32_peak_frac_whole_step": step_fp32 / peak,
+            "roofline": {"bound": "alu", "kernel": f"k_pairs<{name}>", "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "frac_at_load_clock": achieved / peak_load, "traffic": traffic,
+                         "peak_source": f"{SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 x {sm_max:.0f} MHz"},
+            "plain": plain,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "gpu_launches": launches_per_segment(MD_PER_STEP) * args.steps,
+            "clocks": clk,
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def read_traffic(name):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if any."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 2 and parts[0] == name:
+            try:
+                return float(parts[1])
+            except ValueError:
+                return None
+    return None
+
+
+def plain_form(pkg, b, dev, params, n_bench):
+    """Each replica in its own context, MD + MC one step at a time with direct
+    launches (no graph, no batching); same arithmetic.  Exchanges are O(M)
+    and left out of this form."""
+    import synth
+    import torch
+    setups = []
+    for r, rep in enumerate(b.replicas):
+        sb = synth.Batch([rep], pH=b.pH[r:r + 1], E=b.E[r:r + 1], E_ladder=b.E[r:r + 1])
+        S = Setup(pkg, sb, dev, seed=99 + r, params=params)
+        S.st.ex_every = 0
+        setups.append(S)
+    for S in setups:
+        S.ctx.md_segment(S.st, S.sites, 10)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(n_bench):
+        for t in range(MD_PER_STEP):
+            for S in setups:
+                S.ctx.md_segment(S.st, S.sites, 1)
+    e1.record()
+    torch.cuda.synchronize()
+    s = e0.elapsed_time(e1) / 1000.0
+    pairs = b.pairs_per_eval() * MD_PER_STEP * n_bench
+    return {"value": pairs / s, "unit": "pair-interactions/s", "ms_per_step": 1000 * s / n_bench,
+            "replica_md_steps_per_s": b.n_rep * MD_PER_STEP * n_bench / s,
+            "form": "one context per replica, direct launches per MD step, no graph"}
+
+
+def end_to_end(pkg, S, dev, n_bench, pairs_md):
+    """Same metric through the public API with host buffers: every step copies
+    the MD state from pinned host memory, runs the segment and copies the new
+    state back."""
+    import torch
+    host = {k: getattr(S, k).detach().cpu().pin_memory() for k in ("xyzq", "vel", "force", "state", "E")}
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    d2h = h2d
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(n_bench):
+        for k, t in host.items():
+            getattr(S, k).copy_(t, non_blocking=True)
+        S.ctx.md_segment(S.st, S.sites, MD_PER_STEP)
+        for k, t in host.items():
+            t.copy_(getattr(S, k), non_blocking=True)
+        # the result is read on the host every step
+    e1.record(stream)
+    torch.cuda.synchronize()
+    s = e0.elapsed_time(e1) / 1000.0
+    return {"value": pairs_md * MD_PER_STEP * n_bench / s, "unit": "pair-interactions/s",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": n_bench}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,258 @@
+/*
+ * gbremd.h -- C ABI of the GB300 hot path of discrete-state constant redox
+ * potential MD (CEMD), coupled constant pH / redox potential MD (C(pH,E)MD)
+ * and redox-potential replica exchange (E-REMD) in Generalized Born implicit
+ * solvent (Cruzeiro, Amaral, Roitberg, "Redox Potential Replica Exchange
+ * Molecular Dynamics at Constant pH in AMBER").
+ *
+ * Conventions shared by every call
+ *  - Units: kcal/mol, Angstrom, elementary charge e, ps, amu, V, K.
+ *  - A batch holds M replicas (independent molecules) packed back to back;
+ *    replica r owns atoms [atom_off[r], atom_off[r+1]) of every per-atom array.
+ *  - Array arguments are DEVICE pointers owned by the caller unless marked
+ *    "host".  The library owns only what gb_ctx_create allocates (workspace,
+ *    work lists, captured graphs) and frees it in gb_ctx_destroy.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Every call only enqueues work on that stream and returns; outputs are
+ *    valid once the stream reaches that point.
+ *  - Return value: GB_OK (0) or a negative GB_ERR_* code.  Argument and launch
+ *    errors are reported synchronously; gb_last_error() has the message.
+ *    Errors detected on the device (a bounded wait that gave up, non-finite
+ *    input) set a device error word that gb_sync_status() reads and clears.
+ *  - Per-atom layouts:
+ *      xyzq        float[N][4]   x, y, z, charge q
+ *      rad_screen  float[N][2]   intrinsic radius rho, HCT screening factor S
+ *      forces      float[N][3]   F = -dE/dx
+ *      fixed forces int64[3][N]  components x, then y, then z; F * 2^32,
+ *                                rounded (the accumulators themselves)
+ *  - Arithmetic: FP32 pair terms; int64 fixed-point accumulation of forces,
+ *    Born integrals, dE/dR and dE/dq; FP64 for the O(N) Born-radius
+ *    transform, the per-replica energy totals, the Monte Carlo energy change
+ *    and every acceptance test.
+ */
+#ifndef GBREMD_H
+#define GBREMD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GB_OK 0
+#define GB_ERR_INVALID_ARG (-1)
+#define GB_ERR_CUDA (-2)
+#define GB_ERR_TIMEOUT (-3)
+#define GB_ERR_NONFINITE (-4)
+#define GB_ERR_NOMEM (-5)
+
+typedef struct gb_ctx gb_ctx;
+
+/* Generalized Born model parameters.  The paper runs the OBC model of
+ * Onufriev, Bashford and Case ("igb=2", Sec. III.D) for MD and for every
+ * state-change energy; alpha, beta, gamma rescale the HCT integral into the
+ * effective Born radius, `offset` is subtracted from each intrinsic radius,
+ * eps_in / eps_out are the solute and solvent dielectric constants (no salt,
+ * no cutoff).  rep_k, rep_sigma: optional soft repulsion
+ * rep_k (rep_sigma - r)^2 for r < rep_sigma between atoms more than one
+ * position apart in the chain (0 disables it; MD driver only). */
+typedef struct {
+    float alpha, beta, gamma;
+    float offset;
+    float eps_in, eps_out;
+    float rep_k, rep_sigma;
+} gb_params;
+
+/* Create a context for a fixed batch layout.
+ *   n_rep     number of replicas M (>= 1)
+ *   atom_off  HOST int64[M+1], atom_off[0] = 0, non-decreasing; replicas may
+ *             be empty; total atoms N = atom_off[M] < 2^31
+ *   params    HOST pointer, copied
+ *   device    CUDA device ordinal the context lives on
+ * Allocates device workspace proportional to N and M (about 80 bytes per atom).
+ * Errors: GB_ERR_INVALID_ARG, GB_ERR_NOMEM, GB_ERR_CUDA. */
+int gb_ctx_create(gb_ctx** out, int32_t n_rep, const int64_t* atom_off, const gb_params* params,
+                  int32_t device);
+
+/* Release everything the context owns.  NULL is accepted. */
+int gb_ctx_destroy(gb_ctx* ctx);
+
+/* Message of the last error reported on this context (or, for ctx == NULL, of
+ * the last gb_ctx_create failure in this thread).  Owned by the library. */
+const char* gb_last_error(const gb_ctx* ctx);
+
+/* Read and clear the device error word after synchronising `stream`.
+ * Returns GB_OK or the GB_ERR_* code a kernel recorded. */
+int gb_sync_status(gb_ctx* ctx, void* stream);
+
+/* Tile configuration of the pair kernels: warps per block and block pairs
+ * (32 x 32 atom tiles) per warp task.  gb_autotune times the candidates on
+ * the given inputs and keeps the fastest; gb_set_tiles forces one. */
+int gb_autotune(gb_ctx* ctx, const float* xyzq, const float* rad_screen, void* stream);
+int gb_set_tiles(gb_ctx* ctx, int32_t warps_per_block, int32_t tiles_per_task);
+int gb_get_tiles(const gb_ctx* ctx, int32_t* warps_per_block, int32_t* tiles_per_task);
+
+/* Effective Born radii of every atom (OBC model, Sec. III.D):
+ *   a_i = rho_i - offset,  s_j = S_j a_j
+ *   I_i = sum_{j != i} H(r_ij; a_i, s_j)    (HCT pairwise descreening integral)
+ *   psi_i = a_i I_i
+ *   R_i = 1 / (1/a_i - tanh(alpha psi_i - beta psi_i^2 + gamma psi_i^3) / rho_i)
+ * in:  xyzq float[N][4], rad_screen float[N][2]
+ * out: R_out float[N] */
+int gb_born_radii(gb_ctx* ctx, const float* xyzq, const float* rad_screen, float* R_out,
+                  void* stream);
+
+/* GB + Coulomb energy, forces and charge derivative of every replica at the
+ * Born radii of the given coordinates (the radii are recomputed here because
+ * the force needs the chain rule through them):
+ *   E_GB   = -1/2 (1/eps_in - 1/eps_out) k_e sum_i sum_j q_i q_j / f_ij
+ *   f_ij   = sqrt(r_ij^2 + R_i R_j exp(-r_ij^2 / (4 R_i R_j))),  f_ii = R_i
+ *   E_Coul = (k_e / eps_in) sum_{i<j} q_i q_j / r_ij,   k_e = 332.0522173
+ * plus the soft repulsion of gb_params when enabled.  All outputs are
+ * nullable except that at least one must be given:
+ *   R_out      float[N]       Born radii
+ *   F_fixed    int64[3][N]    forces in 2^-32 kcal/mol/A units
+ *   F_out      float[N][3]    forces
+ *   E_out      double[M][3]   E_GB (self terms included), E_Coul, E_repulsion
+ *   dEdq_out   double[N]      phi_i = dE/dq_i at fixed Born radii; the state
+ *                             change energies of Eq. 8 and 9 are built from it */
+int gb_energy_forces(gb_ctx* ctx, const float* xyzq, const float* rad_screen, float* R_out,
+                     int64_t* F_fixed, float* F_out, double* E_out, double* dEdq_out,
+                     void* stream);
+
+/* Titratable sites (residues whose charge set changes between discrete
+ * protonation or redox states, Sec. II.A, II.B).  All DEVICE arrays except
+ * site_off_host.  Site s belongs to the replica r with
+ * site_off[r] <= s < site_off[r+1].
+ *   site_kind[S]        0 = pH-active, 1 = redox-active
+ *   site_nstates[S]     number of states (>= 2)
+ *   site_atom_off[S+1]  atoms of site s are site_atom_idx[site_atom_off[s] ..]
+ *   site_atom_idx[]     replica-local atom index
+ *   site_state_off[S+1] per-state entries of site s start here (G_ref, n_H, n_e)
+ *   site_q_off[S+1]     charge of site s, state k, site atom a at
+ *                       q_state[site_q_off[s] + k * n_atoms(s) + a]
+ *   G_ref (double)      Delta G_elec,ref term of Eq. 8 / 9 as a per-state value;
+ *                       the change of state k -> k' subtracts G_ref[k'] - G_ref[k]
+ *   n_H, n_e            protons / electrons bound in each state
+ *   pKa_ref, E0_ref     per site (double; E0_ref in V) */
+typedef struct {
+    int32_t n_rep;
+    int32_t n_sites;
+    const int32_t* site_off_host;   /* HOST int32[M+1] */
+    const int32_t* site_off;        /* DEVICE copy */
+    const int32_t* site_kind;
+    const int32_t* site_nstates;
+    const int32_t* site_atom_off;
+    const int32_t* site_atom_idx;
+    const int32_t* site_state_off;
+    const int32_t* site_q_off;
+    const float* q_state;
+    const double* G_ref;
+    const int32_t* n_H;
+    const int32_t* n_e;
+    const double* pKa_ref;
+    const double* E0_ref;
+} gb_sites;
+
+/* One Monte Carlo state-change attempt per replica at fixed Born radii
+ * (implicit-solvent scheme, Sec. III.A.1): a single residue of the requested
+ * kind is picked uniformly, a new state is drawn uniformly from its other
+ * states (Sec. III.A), and
+ *   dG = dE_elec - (G_ref[k'] - G_ref[k])
+ *        + F (E - E0_ref) (n_e[k'] - n_e[k])          redox, Eq. 8
+ *        + kT ln10 (pH - pKa_ref) (n_H[k'] - n_H[k])  protonation, Eq. 9
+ * is accepted iff dG <= 0 or u < exp(-dG/kT).  dE_elec is the exact change of
+ * E_GB + E_Coul for the site's new charges with R held fixed, from the
+ * site rows phi_k and the site-site block.  Random numbers: Philox4x64-10,
+ * key (seed, 0), counter (replica, step, 1 + kind, 0); words 0, 1, 2 choose
+ * the site, the state and u.
+ *   kind       0 protonation attempt, 1 redox attempt (C(pH,E)MD runs the
+ *              protonation attempt first when both fall on a step, Sec. III.A)
+ *   xyzq       updated in place: charges of the site atoms on acceptance
+ *   R          Born radii of these coordinates (gb_born_radii)
+ *   pH, E      double[M] per replica (E in V); kT in kcal/mol
+ *   state_inout int32[S] current state of every site, updated on acceptance
+ *   dG_out     double[M] (nullable), acc_out uint8[M] (nullable); replicas
+ *              without a site of this kind report dG = 0, acc = 0 */
+int redox_ph_mc_step(gb_ctx* ctx, const gb_sites* sites, float* xyzq, const float* R,
+                     const double* pH, const double* E, double kT, uint64_t seed, uint64_t step,
+                     int32_t kind, int32_t* state_inout, double* dG_out, uint8_t* acc_out,
+                     void* stream);
+
+/* Replica exchange between neighbouring slots of one or more ladders
+ * (E-REMD, Eq. 14-15 and Sec. III.B; pH ladders by the same argument with
+ * protons, Eq. 12 analogue).  Ladder l, slot k is occupied by replica
+ * rep_at_slot[l * ladder_stride + k * slot_stride] at value values[k].
+ * Attempt number `attempt` pairs slots (0,1),(2,3),... when even and
+ * (1,2),(3,4),... when odd, plus (len-1, 0) for odd attempts when `wrap` is
+ * set and len is even.  For replica i in slot a and j in slot b:
+ *   Delta = c (values[b] - values[a]) (n_count[i] - n_count[j]),
+ *   c = F/kT for dim 0 (E in V, n_count = electrons), ln 10 for dim 1 (pH,
+ *   n_count = protons);
+ * accepted iff Delta <= 0 or u < exp(-Delta), u from Philox4x64-10 with key
+ * (seed, 0) and counter (l*len + a, attempt, 3, 0).  An accepted pair swaps
+ * the two replicas' slots; value_of_rep (nullable, double[M]) then receives
+ * the new ladder value of both replicas.
+ *   delta_out double[n_ladders*len], acc_out uint8[n_ladders*len] (nullable):
+ *   written at index l*len + a of each pair's first slot, NaN / 0 elsewhere. */
+int eremd_exchange(int32_t n_ladders, int32_t ladder_len, int32_t ladder_stride,
+                   int32_t slot_stride, const double* values, int32_t* rep_at_slot,
+                   const int32_t* n_count, int32_t dim, uint64_t attempt, uint64_t seed,
+                   double kT, int32_t wrap, double* value_of_rep, double* delta_out,
+                   uint8_t* acc_out, void* stream);
+
+/* Electrons (kind 1) or protons (kind 0) bound by each replica's sites in
+ * the given states: n_count_out int32[M]. */
+int gb_count_bound(const gb_sites* sites, const int32_t* state, int32_t kind,
+                   int32_t* n_count_out, void* stream);
+
+/* Langevin MD driver of a whole batch: BAOAB splitting, every replica, with
+ * GB + Coulomb + soft repulsion + harmonic chain bonds k (r - r0)^2 between
+ * atoms i, i+1; Monte Carlo attempts every mc_every steps (protonation then
+ * redox, Sec. III.A) and neighbour exchanges every ex_every steps (Sec.
+ * III.B) along the E ladder (ex_dim 0) or pH ladder (ex_dim 1), alternating
+ * between E and pH lines when ex_dim is 2 (two-dimensional grid).  Noise:
+ * Philox4x64-10, key (seed, 0), counter (replica, step, 4, atom), Box-Muller.
+ * The state buffers are owned by the caller and updated in place. */
+typedef struct {
+    float* xyzq;            /* float[N][4] positions + current charges */
+    float* vel;             /* float[N][4] velocities (A/ps), 4th lane unused */
+    float* force;           /* float[N][4] forces at xyzq, kept between calls */
+    const float* rad_screen;
+    float* R;               /* float[N] Born radii of the last evaluation */
+    int32_t* state;         /* int32[S] site states */
+    double* pH;             /* double[M] per replica, rewritten by pH exchanges */
+    double* E;              /* double[M] per replica (V), rewritten by E exchanges */
+    int32_t* grid;          /* int32[n_pH * n_E] replica at (pH row, E column) */
+    const double* E_ladder; /* double[n_E] */
+    const double* pH_ladder;/* double[n_pH] */
+    int32_t n_E, n_pH;
+    double dt, friction, mass, kT;
+    float bond_k, bond_r0;
+    uint64_t seed;
+    uint64_t step;          /* absolute step counter, advanced by the call */
+    uint64_t attempt;       /* exchange attempt counter, advanced by the call */
+    int32_t mc_every, ex_every, ex_dim, wrap;
+} gb_md_state;
+
+/* Advance the batch by nsteps MD steps.  Step t (1-based, absolute) is
+ * followed by MC attempts when t % mc_every == 0 and by an exchange when
+ * t % ex_every == 0.  Requires state->force to hold the forces at the
+ * incoming coordinates (gb_md_init computes them). */
+int gb_md_init(gb_ctx* ctx, gb_md_state* state, void* stream);
+int gb_md_segment(gb_ctx* ctx, gb_md_state* state, const gb_sites* sites, int64_t nsteps,
+                  void* stream);
+
+/* Kernel timing inside the MD driver.  When enabled, CUDA events are recorded
+ * around the three pair passes of every MD step (inside a captured graph they
+ * become event nodes of the graph).  gb_pass_times waits for the events of the
+ * last enqueued block of steps and returns the mean duration (ms) of each pass:
+ * mean_ms[0] Born integrals, [1] energy / direct forces, [2] chain rule. */
+int gb_set_profiling(gb_ctx* ctx, int32_t enable);
+int gb_pass_times(gb_ctx* ctx, double* mean_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBREMD_H */

@@ -1,0 +1,363 @@
+"""Python binding of libgbremd (GB300 CUDA kernels behind a C ABI).
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+library.  Torch supplies device memory and streams.  There is no CPU
+fallback: importing works anywhere, but the first call raises if the shared
+library has not been built or no CUDA device is present.
+
+Call names follow the C ABI in include/gbremd.h:
+    Context.born_radii       -> gb_born_radii
+    Context.energy_forces    -> gb_energy_forces
+    Context.mc_step          -> redox_ph_mc_step
+    eremd_exchange           -> eremd_exchange
+    Context.md_init / md_segment -> gb_md_init / gb_md_segment
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+from typing import Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(_PKG)
+HEADER = os.path.join(ROOT, "include", "gbremd.h")
+LIB_PATH = os.path.join(_PKG, "_build", "libgbremd.so")
+
+KE = 332.0522173
+KB = 0.0019872043
+FARADAY = 23.0605478
+
+GB_OK = 0
+MAX_SITE_ATOMS = 128      # per titratable site (shared-memory rows of the MC kernel)
+ERRORS = {-1: "GB_ERR_INVALID_ARG", -2: "GB_ERR_CUDA", -3: "GB_ERR_TIMEOUT",
+          -4: "GB_ERR_NONFINITE", -5: "GB_ERR_NOMEM"}
+
+
+class GBError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [(k, C.c_float) for k in
+                ("alpha", "beta", "gamma", "offset", "eps_in", "eps_out", "rep_k", "rep_sigma")]
+
+
+def default_params(**kw) -> Params:
+    """OBC alpha, beta, gamma = 1.0, 0.8, 4.85; offset 0.09 A; eps 1 / 78.5;
+    soft repulsion off."""
+    d = dict(alpha=1.0, beta=0.8, gamma=4.85, offset=0.09, eps_in=1.0, eps_out=78.5,
+             rep_k=0.0, rep_sigma=0.0)
+    d.update(kw)
+    return Params(**d)
+
+
+_P = C.c_void_p
+
+
+class Sites(C.Structure):
+    _fields_ = [("n_rep", C.c_int32), ("n_sites", C.c_int32), ("site_off_host", _P),
+                ("site_off", _P), ("site_kind", _P), ("site_nstates", _P), ("site_atom_off", _P),
+                ("site_atom_idx", _P), ("site_state_off", _P), ("site_q_off", _P), ("q_state", _P),
+                ("G_ref", _P), ("n_H", _P), ("n_e", _P), ("pKa_ref", _P), ("E0_ref", _P)]
+
+
+class MDState(C.Structure):
+    _fields_ = [("xyzq", _P), ("vel", _P), ("force", _P), ("rad_screen", _P), ("R", _P),
+                ("state", _P), ("pH", _P), ("E", _P), ("grid", _P), ("E_ladder", _P),
+                ("pH_ladder", _P), ("n_E", C.c_int32), ("n_pH", C.c_int32),
+                ("dt", C.c_double), ("friction", C.c_double), ("mass", C.c_double),
+                ("kT", C.c_double), ("bond_k", C.c_float), ("bond_r0", C.c_float),
+                ("seed", C.c_uint64), ("step", C.c_uint64), ("attempt", C.c_uint64),
+                ("mc_every", C.c_int32), ("ex_every", C.c_int32), ("ex_dim", C.c_int32),
+                ("wrap", C.c_int32)]
+
+
+_lib = None
+
+
+def exported_names() -> list:
+    """Function names declared in include/gbremd.h."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(\w+)\s*\(", src, flags=re.M)))
+
+
+def load(path: Optional[str] = None):
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libgbremd.so not built ({p}); run __graft_entry__.build()")
+    lib = C.CDLL(p)
+    i32, u64, d = C.c_int32, C.c_uint64, C.c_double
+    sig = {
+        "gb_ctx_create": [C.POINTER(_P), i32, _P, C.POINTER(Params), i32],
+        "gb_ctx_destroy": [_P],
+        "gb_sync_status": [_P, _P],
+        "gb_autotune": [_P, _P, _P, _P],
+        "gb_set_tiles": [_P, i32, i32],
+        "gb_get_tiles": [_P, C.POINTER(i32), C.POINTER(i32)],
+        "gb_born_radii": [_P, _P, _P, _P, _P],
+        "gb_energy_forces": [_P, _P, _P, _P, _P, _P, _P, _P, _P],
+        "redox_ph_mc_step": [_P, C.POINTER(Sites), _P, _P, _P, _P, d, u64, u64, i32, _P, _P, _P, _P],
+        "eremd_exchange": [i32, i32, i32, i32, _P, _P, _P, i32, u64, u64, d, i32, _P, _P, _P, _P],
+        "gb_count_bound": [C.POINTER(Sites), _P, i32, _P, _P],
+        "gb_md_init": [_P, C.POINTER(MDState), _P],
+        "gb_md_segment": [_P, C.POINTER(MDState), C.POINTER(Sites), C.c_int64, _P],
+        "gb_set_profiling": [_P, i32],
+        "gb_pass_times": [_P, C.POINTER(C.c_double)],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    lib.gb_last_error.argtypes = [_P]
+    lib.gb_last_error.restype = C.c_char_p
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(rc: int, ctx=None):
+    if rc != GB_OK:
+        msg = load().gb_last_error(ctx).decode(errors="replace")
+        raise GBError(rc, msg)
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+class SiteTables:
+    """Device copies of a site table (see synth.Batch.site_tables) plus the
+    gb_sites struct that points at them."""
+
+    def __init__(self, tables: dict, n_rep: int, device):
+        import torch
+        self.t = {}
+        for k, v in tables.items():
+            if k == "n_sites":
+                continue
+            a = np.asarray(v)
+            dt = {np.dtype(np.int32): torch.int32, np.dtype(np.float32): torch.float32,
+                  np.dtype(np.float64): torch.float64}[a.dtype]
+            self.t[k] = torch.as_tensor(a.copy(), dtype=dt, device=device) if a.size else \
+                torch.zeros(1, dtype=dt, device=device)
+        sizes = np.diff(np.asarray(tables["site_atom_off"]))
+        if sizes.size and (sizes.max() > MAX_SITE_ATOMS or sizes.min() < 1):
+            raise ValueError(f"each site needs 1..{MAX_SITE_ATOMS} atoms")
+        if np.any(np.asarray(tables["site_nstates"]) < 2):
+            raise ValueError("each site needs at least two states")
+        self.site_off_host = np.ascontiguousarray(tables["site_off"], dtype=np.int32)
+        s = Sites()
+        s.n_rep = n_rep
+        s.n_sites = int(tables["n_sites"])
+        s.site_off_host = self.site_off_host.ctypes.data
+        for k in ("site_off", "site_kind", "site_nstates", "site_atom_off", "site_atom_idx",
+                  "site_state_off", "site_q_off", "q_state", "G_ref", "n_H", "n_e", "pKa_ref",
+                  "E0_ref"):
+            setattr(s, k, self.t[k].data_ptr())
+        self.struct = s
+
+    def set_G_ref(self, G):
+        import torch
+        self.t["G_ref"].copy_(torch.as_tensor(np.asarray(G, np.float64)))
+
+
+class Context:
+    """A gb_ctx for a fixed batch layout (atom offsets)."""
+
+    def __init__(self, atom_off: Sequence[int], params: Optional[Params] = None, device: int = 0):
+        self.lib = load()
+        self.atom_off = np.ascontiguousarray(atom_off, dtype=np.int64)
+        self.M = int(self.atom_off.size - 1)
+        self.N = int(self.atom_off[-1])
+        self.params = params or default_params()
+        self.device = device
+        h = _P()
+        rc = self.lib.gb_ctx_create(C.byref(h), self.M, self.atom_off.ctypes.data,
+                                    C.byref(self.params), device)
+        _check(rc, None)
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gb_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- pair passes ----------------------------------------------------------------
+    def born_radii(self, xyzq, rad, R_out=None, stream=None):
+        import torch
+        if R_out is None:
+            R_out = torch.empty(self.N, dtype=torch.float32, device=xyzq.device)
+        _check(self.lib.gb_born_radii(self.h, _ptr(xyzq), _ptr(rad), _ptr(R_out), _stream(stream)), self.h)
+        return R_out
+
+    def energy_forces(self, xyzq, rad, want=("R", "F", "E", "dEdq", "F_fixed"), stream=None):
+        """Returns a dict with the requested outputs (torch tensors)."""
+        import torch
+        dev = xyzq.device
+        out = {}
+        if "R" in want:
+            out["R"] = torch.empty(self.N, dtype=torch.float32, device=dev)
+        if "F" in want:
+            out["F"] = torch.empty((self.N, 3), dtype=torch.float32, device=dev)
+        if "F_fixed" in want:
+            out["F_fixed"] = torch.empty((3, self.N), dtype=torch.int64, device=dev)
+        if "E" in want:
+            out["E"] = torch.empty((self.M, 3), dtype=torch.float64, device=dev)
+        if "dEdq" in want:
+            out["dEdq"] = torch.empty(self.N, dtype=torch.float64, device=dev)
+        rc = self.lib.gb_energy_forces(self.h, _ptr(xyzq), _ptr(rad), _ptr(out.get("R")),
+                                       _ptr(out.get("F_fixed")), _ptr(out.get("F")),
+                                       _ptr(out.get("E")), _ptr(out.get("dEdq")), _stream(stream))
+        _check(rc, self.h)
+        return out
+
+    def sync_status(self, stream=None):
+        _check(self.lib.gb_sync_status(self.h, _stream(stream)), self.h)
+
+    def autotune(self, xyzq, rad, stream=None):
+        _check(self.lib.gb_autotune(self.h, _ptr(xyzq), _ptr(rad), _stream(stream)), self.h)
+        return self.tiles()
+
+    def set_tiles(self, warps_per_block: int, tiles_per_task: int):
+        _check(self.lib.gb_set_tiles(self.h, warps_per_block, tiles_per_task), self.h)
+
+    def tiles(self):
+        w, t = C.c_int32(), C.c_int32()
+        _check(self.lib.gb_get_tiles(self.h, C.byref(w), C.byref(t)), self.h)
+        return int(w.value), int(t.value)
+
+    # -- Monte Carlo ----------------------------------------------------------------
+    def mc_step(self, sites: SiteTables, xyzq, R, pH, E, kT, seed, step, kind, state,
+                dG_out=None, acc_out=None, stream=None):
+        import torch
+        dev = xyzq.device
+        if dG_out is None:
+            dG_out = torch.empty(self.M, dtype=torch.float64, device=dev)
+        if acc_out is None:
+            acc_out = torch.empty(self.M, dtype=torch.uint8, device=dev)
+        rc = self.lib.redox_ph_mc_step(self.h, C.byref(sites.struct), _ptr(xyzq), _ptr(R), _ptr(pH),
+                                       _ptr(E), float(kT), int(seed), int(step), int(kind),
+                                       _ptr(state), _ptr(dG_out), _ptr(acc_out), _stream(stream))
+        _check(rc, self.h)
+        return dG_out, acc_out
+
+    # -- MD ---------------------------------------------------------------------------
+    def md_init(self, st: MDState, stream=None):
+        _check(self.lib.gb_md_init(self.h, C.byref(st), _stream(stream)), self.h)
+
+    def set_profiling(self, on: bool):
+        _check(self.lib.gb_set_profiling(self.h, 1 if on else 0), self.h)
+
+    def pass_times(self):
+        """Mean ms of the Born, energy and chain passes over the last MD block."""
+        arr = (C.c_double * 3)()
+        _check(self.lib.gb_pass_times(self.h, arr), self.h)
+        return [float(v) for v in arr]
+
+    def md_segment(self, st: MDState, sites: Optional[SiteTables], nsteps: int, stream=None):
+        sp = C.byref(sites.struct) if sites is not None else None
+        _check(self.lib.gb_md_segment(self.h, C.byref(st), sp, int(nsteps), _stream(stream)), self.h)
+
+
+def eremd_exchange(values, rep_at_slot, n_count, dim, attempt, seed, kT, wrap=True,
+                   n_ladders=1, ladder_len=None, ladder_stride=None, slot_stride=1,
+                   value_of_rep=None, delta_out=None, acc_out=None, stream=None):
+    import torch
+    lib = load()
+    ladder_len = ladder_len or int(values.numel())
+    ladder_stride = ladder_len if ladder_stride is None else ladder_stride
+    dev = values.device
+    if delta_out is None:
+        delta_out = torch.empty(n_ladders * ladder_len, dtype=torch.float64, device=dev)
+    if acc_out is None:
+        acc_out = torch.empty(n_ladders * ladder_len, dtype=torch.uint8, device=dev)
+    rc = lib.eremd_exchange(n_ladders, ladder_len, ladder_stride, slot_stride, _ptr(values),
+                            _ptr(rep_at_slot), _ptr(n_count), int(dim), int(attempt), int(seed),
+                            float(kT), int(wrap), _ptr(value_of_rep), _ptr(delta_out),
+                            _ptr(acc_out), _stream(stream))
+    _check(rc, None)
+    return delta_out, acc_out
+
+
+def count_bound(sites: SiteTables, state, kind, out=None, stream=None):
+    import torch
+    if out is None:
+        out = torch.empty(sites.struct.n_rep, dtype=torch.int32, device=state.device)
+    _check(load().gb_count_bound(C.byref(sites.struct), _ptr(state), int(kind), _ptr(out),
+                                 _stream(stream)), None)
+    return out
+
+
+class GBEnergy:
+    """torch.autograd.Function over gb_energy_forces: E[M] = E_GB + E_Coul per
+    replica from (xyzq) with backward dE/dx = -F and dE/dq = phi."""
+
+    @staticmethod
+    def apply(ctx_obj: "Context", xyzq, rad):
+        return _GBEnergyFn.apply(xyzq, rad, ctx_obj)
+
+
+def _make_fn():
+    import torch
+
+    class Fn(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, xyzq, rad, gctx):
+            out = gctx.energy_forces(xyzq.detach().contiguous(), rad.contiguous(),
+                                     want=("F", "E", "dEdq"))
+            fctx.save_for_backward(out["F"], out["dEdq"])
+            fctx.atom_off = torch.as_tensor(gctx.atom_off, device=xyzq.device)
+            return (out["E"][:, 0] + out["E"][:, 1])
+
+        @staticmethod
+        def backward(fctx, g):
+            F, phi = fctx.saved_tensors
+            off = fctx.atom_off
+            counts = (off[1:] - off[:-1])
+            g_atom = torch.repeat_interleave(g.to(torch.float64), counts)
+            grad = torch.zeros((F.shape[0], 4), dtype=torch.float32, device=F.device)
+            grad[:, :3] = (-F.double() * g_atom[:, None]).float()
+            grad[:, 3] = (phi * g_atom).float()
+            return grad, None, None
+
+    return Fn
+
+
+class _Lazy:
+    _fn = None
+
+    def __getattr__(self, k):
+        if _Lazy._fn is None:
+            _Lazy._fn = _make_fn()
+        return getattr(_Lazy._fn, k)
+
+
+_GBEnergyFn = _Lazy()

@@ -1,0 +1,762 @@
+// Host side of libgbremd: context, work lists, argument checks, the C ABI.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+using gbk::u64;
+
+struct gb_ctx {
+    int device = 0;
+    int32_t M = 0;
+    int64_t N = 0;
+    int32_t max_n = 0;
+    std::vector<int64_t> off_h;
+    gb_params p{};
+    int64_t* off_d = nullptr;
+    u64* I_acc = nullptr;
+    u64* dR_acc = nullptr;
+    u64* phi_acc = nullptr;
+    u64* F_acc = nullptr;
+    u64* E_acc = nullptr;
+    u64* ctr = nullptr;
+    float2* Rh = nullptr;
+    float* cfac = nullptr;
+    float* cc = nullptr;
+    int* err = nullptr;
+    gbk::TaskList tasks;
+    int wpb = 8;
+    int tpt = 0;
+    int64_t total_tiles = 0;
+    std::string msg;
+    cudaStream_t cs = nullptr;          // private stream for graph capture
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // per-pass timing events inside the MD driver (2 per pass per step)
+    bool prof = false;
+    std::vector<cudaEvent_t> prof_ev;
+    int64_t prof_steps = 0;
+    bool capturing = false;
+    // cached MD graph
+    cudaGraphExec_t md_exec = nullptr;
+    std::vector<uint8_t> md_key;
+    int64_t md_len = 0;
+};
+
+static thread_local std::string g_create_error;
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int fail(gb_ctx* c, int code, const std::string& m) {
+    if (c) c->msg = m;
+    else g_create_error = m;
+    return code;
+}
+
+int cuda_fail(gb_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, GB_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define GB_CHECK(c, call)                                                  \
+    do {                                                                   \
+        cudaError_t e_ = (call);                                           \
+        if (e_ != cudaSuccess) return cuda_fail((c), e_, #call);           \
+    } while (0)
+
+template <class T>
+cudaError_t zalloc(T** p, size_t n) {
+    cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(n, 1) * sizeof(T));
+    if (e != cudaSuccess) return e;
+    return cudaMemset(*p, 0, std::max<size_t>(n, 1) * sizeof(T));
+}
+
+// Cut the upper-triangle tile pairs of all replicas (row-major per replica,
+// replicas in order) into runs of `tpt` tile pairs, one warp task each.
+int build_tasks(gb_ctx* c) {
+    std::vector<int4> t;
+    t.reserve((size_t)(c->total_tiles / c->tpt + 1));
+    int64_t left_total = c->total_tiles;
+    int r = 0, I = 0, J = 0;
+    auto nb_of = [&](int rr) { return (int)((c->off_h[rr + 1] - c->off_h[rr] + 31) / 32); };
+    while (r < c->M && nb_of(r) == 0) ++r;
+    while (left_total > 0) {
+        const int cnt = (int)std::min<int64_t>(c->tpt, left_total);
+        t.push_back(make_int4(r, I, J, cnt));
+        left_total -= cnt;
+        int64_t k = cnt;
+        while (k > 0 && r < c->M) {
+            const int nb = nb_of(r);
+            const int rowleft = nb - J;
+            if (k < rowleft) {
+                J += (int)k;
+                k = 0;
+            } else {
+                k -= rowleft;
+                ++I;
+                J = I;
+                if (I == nb) {
+                    ++r;
+                    while (r < c->M && nb_of(r) == 0) ++r;
+                    I = 0;
+                    J = 0;
+                }
+            }
+        }
+    }
+    if (c->tasks.d_tasks) cudaFree(c->tasks.d_tasks);
+    c->tasks.d_tasks = nullptr;
+    c->tasks.n_tasks = (int)t.size();
+    GB_CHECK(c, zalloc(&c->tasks.d_tasks, t.size()));
+    if (!t.empty())
+        GB_CHECK(c, cudaMemcpy(c->tasks.d_tasks, t.data(), t.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    return GB_OK;
+}
+
+int default_tpt(const gb_ctx* c) {
+    // about four warp tasks per resident warp slot of 152 SMs x 32 warps
+    const int64_t slots = 152LL * 32 * 4;
+    int64_t t = (c->total_tiles + slots - 1) / slots;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(t, 256));
+}
+
+gbk::PairArgs pair_args(const gb_ctx* c, const float* xyzq, const float* rad) {
+    gbk::PairArgs a{};
+    a.atom_off = c->off_d;
+    a.xyzq = (const float4*)xyzq;
+    a.rad = (const float2*)rad;
+    a.Rh = c->Rh;
+    a.cc = c->cc;
+    a.offset = c->p.offset;
+    a.tau_ke = (float)((1.0 / c->p.eps_in - 1.0 / c->p.eps_out) * gbk::KE);
+    a.kc = (float)(gbk::KE / c->p.eps_in);
+    a.rep_k = c->p.rep_k;
+    a.rep_sigma = c->p.rep_sigma;
+    a.I_acc = c->I_acc;
+    a.dR_acc = c->dR_acc;
+    a.phi_acc = c->phi_acc;
+    a.F_acc = c->F_acc;
+    a.E_acc = c->E_acc;
+    a.N = c->N;
+    return a;
+}
+
+gbk::AtomArgs atom_args(const gb_ctx* c, const float* xyzq, const float* rad) {
+    gbk::AtomArgs a{};
+    a.atom_off = c->off_d;
+    a.M = c->M;
+    a.max_n = c->max_n;
+    a.xyzq = (const float4*)xyzq;
+    a.rad = (const float2*)rad;
+    a.alpha = c->p.alpha;
+    a.beta = c->p.beta;
+    a.gamma = c->p.gamma;
+    a.offset = c->p.offset;
+    a.tau_ke = (1.0 / c->p.eps_in - 1.0 / c->p.eps_out) * gbk::KE;
+    a.I_acc = c->I_acc;
+    a.dR_acc = c->dR_acc;
+    a.phi_acc = c->phi_acc;
+    a.F_acc = c->F_acc;
+    a.E_acc = c->E_acc;
+    a.Rh = c->Rh;
+    a.cfac = c->cfac;
+    a.cc = c->cc;
+    a.err = c->err;
+    a.N = c->N;
+    return a;
+}
+
+// The three passes of one energy/force evaluation.  flags: gbk::EF_*.
+cudaError_t mark(gb_ctx* c, cudaEvent_t e, cudaStream_t s) {
+    return c->capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
+}
+
+int evaluate(gb_ctx* c, const float* xyzq, const float* rad, float* R_out, int flags,
+             double* phi_out, cudaStream_t s, const cudaEvent_t* ev = nullptr) {
+    const gbk::PairArgs pa = pair_args(c, xyzq, rad);
+    const gbk::AtomArgs aa = atom_args(c, xyzq, rad);
+    if (ev) GB_CHECK(c, mark(c, ev[0], s));
+    GB_CHECK(c, gbk::launch_pairs(gbk::PASS_BORN, 0, pa, c->tasks, c->wpb, s));
+    if (ev) GB_CHECK(c, mark(c, ev[1], s));
+    GB_CHECK(c, gbk::launch_born_finalize(aa, R_out, s));
+    if (ev) GB_CHECK(c, mark(c, ev[2], s));
+    GB_CHECK(c, gbk::launch_pairs(gbk::PASS_ENERGY, flags, pa, c->tasks, c->wpb, s));
+    if (ev) GB_CHECK(c, mark(c, ev[3], s));
+    GB_CHECK(c, gbk::launch_energy_finalize(aa, (flags & gbk::EF_ENERGY) ? 1 : 0, phi_out, s));
+    if (ev) GB_CHECK(c, mark(c, ev[4], s));
+    GB_CHECK(c, gbk::launch_pairs(gbk::PASS_CHAIN, 0, pa, c->tasks, c->wpb, s));
+    if (ev) GB_CHECK(c, mark(c, ev[5], s));
+    return GB_OK;
+}
+
+int ensure_prof_events(gb_ctx* c, int64_t steps) {
+    while ((int64_t)c->prof_ev.size() < 6 * steps) {
+        cudaEvent_t e;
+        GB_CHECK(c, cudaEventCreate(&e));
+        c->prof_ev.push_back(e);
+    }
+    return GB_OK;
+}
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+int check_sites(gb_ctx* c, const gb_sites* s) {
+    if (!s) return fail(c, GB_ERR_INVALID_ARG, "sites is NULL");
+    if (s->n_rep != c->M) return fail(c, GB_ERR_INVALID_ARG, "sites->n_rep differs from the context's replica count");
+    if (s->n_sites > 0 && (!s->site_off || !s->site_kind || !s->site_nstates || !s->site_atom_off ||
+                           !s->site_atom_idx || !s->site_state_off || !s->site_q_off || !s->q_state ||
+                           !s->G_ref || !s->n_H || !s->n_e || !s->pKa_ref || !s->E0_ref))
+        return fail(c, GB_ERR_INVALID_ARG, "a site table pointer is NULL");
+    if (!s->site_off) return fail(c, GB_ERR_INVALID_ARG, "sites->site_off is NULL");
+    return GB_OK;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------------
+
+extern "C" int gb_ctx_create(gb_ctx** out, int32_t n_rep, const int64_t* atom_off,
+                             const gb_params* params, int32_t device) {
+    if (!out || !atom_off || !params) return fail(nullptr, GB_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (n_rep < 1) return fail(nullptr, GB_ERR_INVALID_ARG, "n_rep must be >= 1");
+    if (atom_off[0] != 0) return fail(nullptr, GB_ERR_INVALID_ARG, "atom_off[0] must be 0");
+    for (int r = 0; r < n_rep; ++r)
+        if (atom_off[r + 1] < atom_off[r]) return fail(nullptr, GB_ERR_INVALID_ARG, "atom_off must be non-decreasing");
+    if (atom_off[n_rep] >= (1LL << 31)) return fail(nullptr, GB_ERR_INVALID_ARG, "too many atoms");
+    if (!(params->offset >= 0.0f) || !(params->eps_in > 0.0f) || !(params->eps_out > 0.0f) ||
+        !(params->rep_k >= 0.0f) || !(params->rep_sigma >= 0.0f))
+        return fail(nullptr, GB_ERR_INVALID_ARG, "invalid GB parameters");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return fail(nullptr, GB_ERR_CUDA, "no such CUDA device");
+    DeviceGuard g(device);
+    gb_ctx* c = new gb_ctx();
+    c->device = device;
+    c->M = n_rep;
+    c->off_h.assign(atom_off, atom_off + n_rep + 1);
+    c->N = atom_off[n_rep];
+    c->p = *params;
+    for (int r = 0; r < n_rep; ++r) {
+        const int64_t n = atom_off[r + 1] - atom_off[r];
+        c->max_n = (int32_t)std::max<int64_t>(c->max_n, n);
+        const int64_t nb = (n + 31) / 32;
+        c->total_tiles += nb * (nb + 1) / 2;
+    }
+    const size_t N = (size_t)c->N;
+    cudaError_t e = cudaSuccess;
+    auto step = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+    step(zalloc(&c->off_d, n_rep + 1));
+    step(cudaMemcpy(c->off_d, atom_off, sizeof(int64_t) * (n_rep + 1), cudaMemcpyHostToDevice));
+    step(zalloc(&c->I_acc, N));
+    step(zalloc(&c->dR_acc, N));
+    step(zalloc(&c->phi_acc, N));
+    step(zalloc(&c->F_acc, 3 * N));
+    step(zalloc(&c->E_acc, 4 * (size_t)n_rep));
+    step(zalloc(&c->ctr, 2));
+    step(zalloc(&c->Rh, N));
+    step(zalloc(&c->cfac, N));
+    step(zalloc(&c->cc, N));
+    step(zalloc(&c->err, 1));
+    step(cudaStreamCreateWithFlags(&c->cs, cudaStreamNonBlocking));
+    step(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+    step(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
+    if (e != cudaSuccess) {
+        int code = (e == cudaErrorMemoryAllocation) ? GB_ERR_NOMEM : GB_ERR_CUDA;
+        fail(nullptr, code, std::string("context allocation: ") + cudaGetErrorString(e));
+        gb_ctx_destroy(c);
+        return code;
+    }
+    c->tpt = default_tpt(c);
+    int rc = build_tasks(c);
+    if (rc != GB_OK) {
+        g_create_error = c->msg;
+        gb_ctx_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return GB_OK;
+}
+
+extern "C" int gb_ctx_destroy(gb_ctx* c) {
+    if (!c) return GB_OK;
+    DeviceGuard g(c->device);
+    if (c->md_exec) cudaGraphExecDestroy(c->md_exec);
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    cudaFree(c->tasks.d_tasks);
+    cudaFree(c->off_d);
+    cudaFree(c->I_acc);
+    cudaFree(c->dR_acc);
+    cudaFree(c->phi_acc);
+    cudaFree(c->F_acc);
+    cudaFree(c->E_acc);
+    cudaFree(c->ctr);
+    cudaFree(c->Rh);
+    cudaFree(c->cfac);
+    cudaFree(c->cc);
+    cudaFree(c->err);
+    if (c->cs) cudaStreamDestroy(c->cs);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
+    delete c;
+    return GB_OK;
+}
+
+extern "C" const char* gb_last_error(const gb_ctx* c) {
+    return c ? c->msg.c_str() : g_create_error.c_str();
+}
+
+extern "C" int gb_sync_status(gb_ctx* c, void* stream) {
+    if (!c) return fail(nullptr, GB_ERR_INVALID_ARG, "NULL context");
+    DeviceGuard g(c->device);
+    GB_CHECK(c, cudaStreamSynchronize((cudaStream_t)stream));
+    int h = 0;
+    GB_CHECK(c, cudaMemcpy(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost));
+    GB_CHECK(c, cudaMemset(c->err, 0, sizeof(int)));
+    if (h != 0) return fail(c, h, "error recorded on the device");
+    return GB_OK;
+}
+
+extern "C" int gb_set_tiles(gb_ctx* c, int32_t wpb, int32_t tpt) {
+    if (!c) return fail(nullptr, GB_ERR_INVALID_ARG, "NULL context");
+    if (wpb < 1 || wpb > 8 || tpt < 1 || tpt > (1 << 20))
+        return fail(c, GB_ERR_INVALID_ARG, "warps_per_block must be 1..8, tiles_per_task 1..2^20");
+    DeviceGuard g(c->device);
+    c->wpb = wpb;
+    if (tpt != c->tpt) {
+        GB_CHECK(c, cudaDeviceSynchronize());
+        c->tpt = tpt;
+        int rc = build_tasks(c);
+        if (rc) return rc;
+        if (c->md_exec) { cudaGraphExecDestroy(c->md_exec); c->md_exec = nullptr; c->md_key.clear(); }
+    }
+    return GB_OK;
+}
+
+extern "C" int gb_get_tiles(const gb_ctx* c, int32_t* wpb, int32_t* tpt) {
+    if (!c || !wpb || !tpt) return GB_ERR_INVALID_ARG;
+    *wpb = c->wpb;
+    *tpt = c->tpt;
+    return GB_OK;
+}
+
+static int check_inputs(gb_ctx* c, const float* xyzq, const float* rad) {
+    if (!c) return fail(nullptr, GB_ERR_INVALID_ARG, "NULL context");
+    if (!xyzq || !rad) return fail(c, GB_ERR_INVALID_ARG, "xyzq / rad_screen is NULL");
+    if (!aligned(xyzq, 16) || !aligned(rad, 8))
+        return fail(c, GB_ERR_INVALID_ARG, "xyzq must be 16-byte and rad_screen 8-byte aligned");
+    return GB_OK;
+}
+
+extern "C" int gb_born_radii(gb_ctx* c, const float* xyzq, const float* rad, float* R_out, void* stream) {
+    int rc = check_inputs(c, xyzq, rad);
+    if (rc) return rc;
+    if (!R_out) return fail(c, GB_ERR_INVALID_ARG, "R_out is NULL");
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const gbk::PairArgs pa = pair_args(c, xyzq, rad);
+    const gbk::AtomArgs aa = atom_args(c, xyzq, rad);
+    GB_CHECK(c, gbk::launch_pairs(gbk::PASS_BORN, 0, pa, c->tasks, c->wpb, s));
+    GB_CHECK(c, gbk::launch_born_finalize(aa, R_out, s));
+    return GB_OK;
+}
+
+extern "C" int gb_energy_forces(gb_ctx* c, const float* xyzq, const float* rad, float* R_out,
+                                int64_t* F_fixed, float* F_out, double* E_out, double* dEdq_out,
+                                void* stream) {
+    int rc = check_inputs(c, xyzq, rad);
+    if (rc) return rc;
+    if (!R_out && !F_fixed && !F_out && !E_out && !dEdq_out)
+        return fail(c, GB_ERR_INVALID_ARG, "no output requested");
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int flags = (E_out ? gbk::EF_ENERGY : 0) | (dEdq_out ? gbk::EF_PHI : 0) |
+                (c->p.rep_k != 0.0f ? gbk::EF_REP : 0);
+    rc = evaluate(c, xyzq, rad, R_out, flags, dEdq_out, s);
+    if (rc) return rc;
+    GB_CHECK(c, gbk::launch_forces_out(atom_args(c, xyzq, rad), F_fixed, F_out, E_out, s));
+    return GB_OK;
+}
+
+extern "C" int redox_ph_mc_step(gb_ctx* c, const gb_sites* sites, float* xyzq, const float* R,
+                                const double* pH, const double* E, double kT, uint64_t seed,
+                                uint64_t step, int32_t kind, int32_t* state, double* dG_out,
+                                uint8_t* acc_out, void* stream) {
+    if (!c) return fail(nullptr, GB_ERR_INVALID_ARG, "NULL context");
+    int rc = check_sites(c, sites);
+    if (rc) return rc;
+    if (!xyzq || !R || !pH || !E || !state) return fail(c, GB_ERR_INVALID_ARG, "NULL array");
+    if (kind != 0 && kind != 1) return fail(c, GB_ERR_INVALID_ARG, "kind must be 0 (pH) or 1 (redox)");
+    if (!(kT > 0.0)) return fail(c, GB_ERR_INVALID_ARG, "kT must be positive");
+    if (!aligned(xyzq, 16)) return fail(c, GB_ERR_INVALID_ARG, "xyzq must be 16-byte aligned");
+    DeviceGuard g(c->device);
+    gbk::MCArgs a{};
+    a.atom_off = c->off_d;
+    a.site_off = sites->site_off;
+    a.site_kind = sites->site_kind;
+    a.site_nstates = sites->site_nstates;
+    a.site_atom_off = sites->site_atom_off;
+    a.site_atom_idx = sites->site_atom_idx;
+    a.site_state_off = sites->site_state_off;
+    a.site_q_off = sites->site_q_off;
+    a.q_state = sites->q_state;
+    a.G_ref = sites->G_ref;
+    a.n_H = sites->n_H;
+    a.n_e = sites->n_e;
+    a.pKa_ref = sites->pKa_ref;
+    a.E0_ref = sites->E0_ref;
+    a.xyzq = (float4*)xyzq;
+    a.R = R;
+    a.pH = pH;
+    a.E = E;
+    a.kT = kT;
+    a.tau_ke = (1.0 / c->p.eps_in - 1.0 / c->p.eps_out) * gbk::KE;
+    a.kc = gbk::KE / c->p.eps_in;
+    a.seed = seed;
+    a.step = step;
+    a.ctr = nullptr;
+    a.kind = kind;
+    a.state = state;
+    a.dG_out = dG_out;
+    a.acc_out = acc_out;
+    GB_CHECK(c, gbk::launch_mc(a, c->M, (cudaStream_t)stream));
+    return GB_OK;
+}
+
+extern "C" int eremd_exchange(int32_t n_ladders, int32_t len, int32_t ladder_stride,
+                              int32_t slot_stride, const double* values, int32_t* rep_at_slot,
+                              const int32_t* n_count, int32_t dim, uint64_t attempt, uint64_t seed,
+                              double kT, int32_t wrap, double* value_of_rep, double* delta_out,
+                              uint8_t* acc_out, void* stream) {
+    if (n_ladders < 0 || len < 0 || !values || !rep_at_slot || !n_count)
+        return fail(nullptr, GB_ERR_INVALID_ARG, "invalid exchange arguments");
+    if (dim != 0 && dim != 1) return fail(nullptr, GB_ERR_INVALID_ARG, "dim must be 0 (E) or 1 (pH)");
+    if (!(kT > 0.0)) return fail(nullptr, GB_ERR_INVALID_ARG, "kT must be positive");
+    gbk::ExArgs a{};
+    a.n_ladders = n_ladders;
+    a.len = len;
+    a.ladder_stride = ladder_stride;
+    a.slot_stride = slot_stride;
+    a.values = values;
+    a.rep_at_slot = rep_at_slot;
+    a.n_count = n_count;
+    a.dim = dim;
+    a.attempt = attempt;
+    a.ctr = nullptr;
+    a.seed = seed;
+    a.kT = kT;
+    a.wrap = wrap;
+    a.value_of_rep = value_of_rep;
+    a.delta_out = delta_out;
+    a.acc_out = acc_out;
+    cudaError_t e = gbk::launch_exchange(a, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(nullptr, GB_ERR_CUDA, cudaGetErrorString(e));
+    return GB_OK;
+}
+
+extern "C" int gb_count_bound(const gb_sites* s, const int32_t* state, int32_t kind,
+                              int32_t* out, void* stream) {
+    if (!s || !state || !out || !s->site_off) return fail(nullptr, GB_ERR_INVALID_ARG, "NULL argument");
+    cudaError_t e = gbk::launch_count(s->site_off, s->site_kind, s->site_state_off, s->n_H, s->n_e,
+                                      state, kind, s->n_rep, out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(nullptr, GB_ERR_CUDA, cudaGetErrorString(e));
+    return GB_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// MD driver
+
+namespace {
+
+gbk::MDArgs md_args(const gb_ctx* c, const gb_md_state* st) {
+    gbk::MDArgs m{};
+    m.xyzq = (float4*)st->xyzq;
+    m.vel = (float4*)st->vel;
+    m.force = (float4*)st->force;
+    m.ctr = c->ctr;
+    m.h = (float)(0.5 * st->dt);
+    m.inv_m = (float)(gbk::ACCEL / st->mass);
+    const double c1 = std::exp(-st->friction * st->dt);
+    m.c1 = (float)c1;
+    m.c2 = (float)std::sqrt((1.0 - c1 * c1) * st->kT * gbk::ACCEL / st->mass);
+    m.bond_k = st->bond_k;
+    m.bond_r0 = st->bond_r0;
+    m.seed = st->seed;
+    return m;
+}
+
+int check_md(gb_ctx* c, const gb_md_state* st) {
+    if (!c) return fail(nullptr, GB_ERR_INVALID_ARG, "NULL context");
+    if (!st || !st->xyzq || !st->vel || !st->force || !st->rad_screen)
+        return fail(c, GB_ERR_INVALID_ARG, "MD state buffer is NULL");
+    if (!aligned(st->xyzq, 16) || !aligned(st->vel, 16) || !aligned(st->force, 16))
+        return fail(c, GB_ERR_INVALID_ARG, "MD buffers must be 16-byte aligned");
+    if (!(st->dt > 0) || !(st->mass > 0) || !(st->kT > 0) || !(st->friction >= 0))
+        return fail(c, GB_ERR_INVALID_ARG, "invalid MD constants");
+    return GB_OK;
+}
+
+// Enqueue `len` MD steps (with their MC attempts and exchanges) on stream s.
+// Steps are numbered from the device counter ctr[0]; the last node advances it.
+int enqueue_steps(gb_ctx* c, gb_md_state* st, const gb_sites* sites, int64_t len, cudaStream_t s) {
+    const float* xyzq = st->xyzq;
+    const float* rad = st->rad_screen;
+    const gbk::AtomArgs aa = atom_args(c, xyzq, rad);
+    const gbk::MDArgs m = md_args(c, st);
+    const int flags = (c->p.rep_k != 0.0f) ? gbk::EF_REP : 0;
+    int64_t n_ex = 0;
+    if (c->prof) {
+        int rc = ensure_prof_events(c, len);
+        if (rc) return rc;
+        c->prof_steps = len;
+    }
+    for (int64_t k = 0; k < len; ++k) {
+        GB_CHECK(c, gbk::launch_md_first(aa, m, (int)k, s));
+        int rc = evaluate(c, xyzq, rad, st->R, flags, nullptr, s,
+                          c->prof ? &c->prof_ev[6 * k] : nullptr);
+        if (rc) return rc;
+        GB_CHECK(c, gbk::launch_md_second(aa, m, s));
+        const int64_t t = (int64_t)st->step + k + 1;   // only its residues matter
+        if (sites && st->mc_every > 0 && t % st->mc_every == 0) {
+            for (int kind = 0; kind < 2; ++kind) {
+                gbk::MCArgs a{};
+                a.atom_off = c->off_d;
+                a.site_off = sites->site_off;
+                a.site_kind = sites->site_kind;
+                a.site_nstates = sites->site_nstates;
+                a.site_atom_off = sites->site_atom_off;
+                a.site_atom_idx = sites->site_atom_idx;
+                a.site_state_off = sites->site_state_off;
+                a.site_q_off = sites->site_q_off;
+                a.q_state = sites->q_state;
+                a.G_ref = sites->G_ref;
+                a.n_H = sites->n_H;
+                a.n_e = sites->n_e;
+                a.pKa_ref = sites->pKa_ref;
+                a.E0_ref = sites->E0_ref;
+                a.xyzq = (float4*)st->xyzq;
+                a.R = nullptr;
+                a.Rh = c->Rh;
+                a.pH = st->pH;
+                a.E = st->E;
+                a.kT = st->kT;
+                a.tau_ke = (1.0 / c->p.eps_in - 1.0 / c->p.eps_out) * gbk::KE;
+                a.kc = gbk::KE / c->p.eps_in;
+                a.seed = st->seed;
+                a.step = (u64)(k + 1);
+                a.ctr = c->ctr;
+                a.kind = kind;
+                a.state = st->state;
+                a.dG_out = nullptr;
+                a.acc_out = nullptr;
+                GB_CHECK(c, gbk::launch_mc(a, c->M, s));
+            }
+        }
+        if (sites && st->grid && st->ex_every > 0 && t % st->ex_every == 0) {
+            gbk::GridExArgs x{};
+            x.n_pH = st->n_pH;
+            x.n_E = st->n_E;
+            x.E_ladder = st->E_ladder;
+            x.pH_ladder = st->pH_ladder;
+            x.grid = st->grid;
+            x.site_off = sites->site_off;
+            x.site_kind = sites->site_kind;
+            x.site_state_off = sites->site_state_off;
+            x.n_H = sites->n_H;
+            x.n_e = sites->n_e;
+            x.state = st->state;
+            x.ctr = c->ctr;
+            x.ex_dim = st->ex_dim;
+            x.wrap = st->wrap;
+            x.seed = st->seed;
+            x.kT = st->kT;
+            x.E_rep = st->E;
+            x.pH_rep = st->pH;
+            GB_CHECK(c, gbk::launch_grid_exchange(x, s));
+            GB_CHECK(c, gbk::launch_advance_counters(c->ctr, 0, 1, s));
+            ++n_ex;
+        }
+    }
+    GB_CHECK(c, gbk::launch_advance_counters(c->ctr, (u64)len, 0, s));
+    return GB_OK;
+}
+
+}  // namespace
+
+extern "C" int gb_md_init(gb_ctx* c, gb_md_state* st, void* stream) {
+    int rc = check_md(c, st);
+    if (rc) return rc;
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int flags = (c->p.rep_k != 0.0f) ? gbk::EF_REP : 0;
+    rc = evaluate(c, st->xyzq, st->rad_screen, st->R, flags, nullptr, s);
+    if (rc) return rc;
+    GB_CHECK(c, gbk::launch_md_force_only(atom_args(c, st->xyzq, st->rad_screen), md_args(c, st), s));
+    return GB_OK;
+}
+
+extern "C" int gb_md_segment(gb_ctx* c, gb_md_state* st, const gb_sites* sites, int64_t nsteps,
+                             void* stream) {
+    int rc = check_md(c, st);
+    if (rc) return rc;
+    if (nsteps < 0) return fail(c, GB_ERR_INVALID_ARG, "nsteps < 0");
+    if (sites) {
+        rc = check_sites(c, sites);
+        if (rc) return rc;
+        if (st->mc_every > 0 && !st->state) return fail(c, GB_ERR_INVALID_ARG, "state is NULL");
+        if (st->ex_every > 0 && st->grid &&
+            (st->n_E * st->n_pH != c->M || !st->E_ladder || !st->pH_ladder || !st->E || !st->pH))
+            return fail(c, GB_ERR_INVALID_ARG, "exchange grid does not match the batch");
+    }
+    if (nsteps == 0) return GB_OK;
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    // one captured block covers a whole number of MC and exchange periods
+    int64_t L = 1;
+    auto lcm = [](int64_t a, int64_t b) {
+        int64_t x = a, y = b;
+        while (y) { int64_t t = x % y; x = y; y = t; }
+        return a / x * b;
+    };
+    if (sites && st->mc_every > 0) L = lcm(L, st->mc_every);
+    if (sites && st->grid && st->ex_every > 0) L = lcm(L, st->ex_every);
+    const bool graph_ok = (L <= 1000) && ((int64_t)st->step % L == 0) && (nsteps % L == 0);
+    GB_CHECK(c, gbk::launch_set_counters(c->ctr, st->step, st->attempt, s));
+    if (!graph_ok) {
+        rc = enqueue_steps(c, st, sites, nsteps, s);
+        if (rc) return rc;
+    } else {
+        // key: everything baked into the graph
+        std::vector<uint8_t> key(sizeof(gb_md_state) + sizeof(gb_sites) + sizeof(int64_t) * 3);
+        gb_md_state kst = *st;
+        kst.step = 0;
+        kst.attempt = 0;
+        memcpy(key.data(), &kst, sizeof(kst));
+        gb_sites ks{};
+        if (sites) ks = *sites;
+        memcpy(key.data() + sizeof(kst), &ks, sizeof(ks));
+        const int64_t extra[3] = {L, c->wpb, (int64_t)c->tpt * 2 + (c->prof ? 1 : 0)};
+        memcpy(key.data() + sizeof(kst) + sizeof(ks), extra, sizeof(extra));
+        if (c->prof) {
+            rc = ensure_prof_events(c, L);
+            if (rc) return rc;
+        }
+        if (!c->md_exec || key != c->md_key) {
+            if (c->md_exec) { cudaGraphExecDestroy(c->md_exec); c->md_exec = nullptr; }
+            cudaGraph_t graph = nullptr;
+            GB_CHECK(c, cudaStreamBeginCapture(c->cs, cudaStreamCaptureModeThreadLocal));
+            c->capturing = true;
+            rc = enqueue_steps(c, st, sites, L, c->cs);
+            c->capturing = false;
+            cudaError_t e = cudaStreamEndCapture(c->cs, &graph);
+            if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+            if (e != cudaSuccess) return cuda_fail(c, e, "graph capture");
+            e = cudaGraphInstantiate(&c->md_exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) { c->md_exec = nullptr; return cuda_fail(c, e, "graph instantiate"); }
+            c->md_key = key;
+            c->md_len = L;
+        }
+        GB_CHECK(c, cudaEventRecord(c->ev_in, s));
+        GB_CHECK(c, cudaStreamWaitEvent(c->cs, c->ev_in, 0));
+        for (int64_t k = 0; k < nsteps / L; ++k) GB_CHECK(c, cudaGraphLaunch(c->md_exec, c->cs));
+        GB_CHECK(c, cudaEventRecord(c->ev_out, c->cs));
+        GB_CHECK(c, cudaStreamWaitEvent(s, c->ev_out, 0));
+    }
+    int64_t n_ex = 0;
+    if (sites && st->grid && st->ex_every > 0)
+        n_ex = ((int64_t)st->step + nsteps) / st->ex_every - (int64_t)st->step / st->ex_every;
+    st->step += (uint64_t)nsteps;
+    st->attempt += (uint64_t)n_ex;
+    return GB_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Autotuner: time one full force evaluation per candidate tile shape.
+
+extern "C" int gb_autotune(gb_ctx* c, const float* xyzq, const float* rad, void* stream) {
+    int rc = check_inputs(c, xyzq, rad);
+    if (rc) return rc;
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    GB_CHECK(c, cudaStreamSynchronize(s));
+    const int wpbs[] = {4, 8};
+    std::vector<int> tpts;
+    const int base = default_tpt(c);
+    for (int f : {1, 2, 4, 8, 16}) {
+        int t = std::max(1, base * f / 4);
+        if (std::find(tpts.begin(), tpts.end(), t) == tpts.end()) tpts.push_back(t);
+    }
+    cudaEvent_t e0, e1;
+    GB_CHECK(c, cudaEventCreate(&e0));
+    GB_CHECK(c, cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_w = c->wpb, best_t = c->tpt;
+    for (int t : tpts) {
+        rc = gb_set_tiles(c, c->wpb, t);
+        if (rc) break;
+        for (int w : wpbs) {
+            c->wpb = w;
+            float ms_min = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, s);
+                rc = evaluate(c, xyzq, rad, nullptr, 0, nullptr, s);
+                if (rc) break;
+                rc = gbk::launch_forces_out(atom_args(c, xyzq, rad), nullptr, nullptr, nullptr, s) ==
+                             cudaSuccess ? GB_OK : GB_ERR_CUDA;
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) ms_min = std::min(ms_min, ms);
+            }
+            if (rc) break;
+            if (ms_min < best) { best = ms_min; best_w = w; best_t = t; }
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    return gb_set_tiles(c, best_w, best_t);
+}
+
+extern "C" int gb_set_profiling(gb_ctx* c, int32_t enable) {
+    if (!c) return fail(nullptr, GB_ERR_INVALID_ARG, "NULL context");
+    c->prof = enable != 0;
+    c->prof_steps = 0;
+    return GB_OK;
+}
+
+extern "C" int gb_pass_times(gb_ctx* c, double* mean_ms) {
+    if (!c || !mean_ms) return fail(c, GB_ERR_INVALID_ARG, "NULL argument");
+    if (!c->prof || c->prof_steps == 0) return fail(c, GB_ERR_INVALID_ARG, "profiling is off or no segment ran");
+    DeviceGuard g(c->device);
+    for (int p = 0; p < 3; ++p) {
+        double acc = 0.0;
+        for (int64_t k = 0; k < c->prof_steps; ++k) {
+            float ms = 0.0f;
+            GB_CHECK(c, cudaEventSynchronize(c->prof_ev[6 * k + 2 * p + 1]));
+            GB_CHECK(c, cudaEventElapsedTime(&ms, c->prof_ev[6 * k + 2 * p], c->prof_ev[6 * k + 2 * p + 1]));
+            acc += ms;
+        }
+        mean_ms[p] = acc / (double)c->prof_steps;
+    }
+    return GB_OK;
+}

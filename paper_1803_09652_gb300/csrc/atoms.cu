@@ -1,0 +1,507 @@
+// O(N) and O(sites x N) kernels: Born-radius transform, self terms and
+// readout of the fixed-point accumulators, BAOAB half steps, Monte Carlo state
+// changes (Eq. 8, 9), replica exchange (Eq. 14, 15).
+#include <cmath>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace gbk {
+
+__device__ __forceinline__ double block_sum_d(double v, double* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[k];
+    return t;  // valid in thread 0
+}
+
+__device__ __forceinline__ void set_err(int* err, int code) { atomicCAS(err, 0, code); }
+
+// --- Born radii: I -> psi -> R (OBC), FP64 ------------------------------------
+__global__ void k_born_finalize(AtomArgs A, float* R_out) {
+    const int r = blockIdx.y;
+    const int64_t base = A.atom_off[r];
+    const int n = (int)(A.atom_off[r + 1] - base);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t g = base + i;
+    const double I = (double)(long long)A.I_acc[g] * FIX_I_INV;
+    A.I_acc[g] = 0;
+    const float2 rs = A.rad[g];
+    const double rho = rs.x;
+    const double a = rho - (double)A.offset;
+    const double psi = a * I;
+    const double al = A.alpha, be = A.beta, ga = A.gamma;
+    const double th = tanh(psi * (al + psi * (-be + ga * psi)));
+    const double R = 1.0 / (1.0 / a - th / rho);
+    const double dRdpsi = R * R * (1.0 - th * th) * (al - 2.0 * be * psi + 3.0 * ga * psi * psi) / rho;
+    if (!(R > 0.0) || !isfinite(R) || !isfinite(dRdpsi)) set_err(A.err, GB_ERR_NONFINITE);
+    A.Rh[g] = make_float2((float)R, (float)(0.5 / R));
+    A.cfac[g] = (float)(dRdpsi * a);
+    if (R_out) R_out[g] = (float)R;
+}
+
+// --- self terms, dE/dR -> chain factor, dE/dq readout ----------------------------
+__global__ void k_energy_finalize(AtomArgs A, int want_energy, double* phi_out) {
+    __shared__ double sh[32];
+    const int r = blockIdx.y;
+    const int64_t base = A.atom_off[r];
+    const int n = (int)(A.atom_off[r + 1] - base);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double eself = 0.0;
+    if (i < n) {
+        const int64_t g = base + i;
+        const double q = A.xyzq[g].w;
+        const double R = A.Rh[g].x;
+        const double dEdR = unfix(A.dR_acc[g]) + 0.5 * A.tau_ke * q * q / (R * R);
+        A.dR_acc[g] = 0;
+        A.cc[g] = (float)(dEdR * (double)A.cfac[g]);
+        eself = -0.5 * A.tau_ke * q * q / R;
+        if (phi_out) {
+            phi_out[g] = unfix(A.phi_acc[g]) - A.tau_ke * q / R;
+            A.phi_acc[g] = 0;
+        }
+    }
+    if (want_energy) {
+        if (blockIdx.x * blockDim.x >= (unsigned)n) return;
+        const double t = block_sum_d(eself, sh);
+        if (threadIdx.x == 0) red_add(&A.E_acc[4 * r + 0], fix_d(t));
+    }
+}
+
+// --- readout: int64 forces -> outputs; energies -> FP64; clear accumulators -------
+__global__ void k_forces_out(AtomArgs A, int64_t* F_fixed, float* F_out, double* E_out) {
+    const int r = blockIdx.y;
+    const int64_t base = A.atom_off[r];
+    const int n = (int)(A.atom_off[r + 1] - base);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.x == 0 && threadIdx.x < 3) {
+        if (E_out) E_out[3 * r + threadIdx.x] = unfix(A.E_acc[4 * r + threadIdx.x]);
+        A.E_acc[4 * r + threadIdx.x] = 0;
+    }
+    if (i >= n) return;
+    const int64_t g = base + i;
+    const u64 fx = A.F_acc[g], fy = A.F_acc[A.N + g], fz = A.F_acc[2 * A.N + g];
+    A.F_acc[g] = 0;
+    A.F_acc[A.N + g] = 0;
+    A.F_acc[2 * A.N + g] = 0;
+    if (F_fixed) {
+        F_fixed[g] = (long long)fx;
+        F_fixed[A.N + g] = (long long)fy;
+        F_fixed[2 * A.N + g] = (long long)fz;
+    }
+    if (F_out) {
+        F_out[3 * g + 0] = (float)unfix(fx);
+        F_out[3 * g + 1] = (float)unfix(fy);
+        F_out[3 * g + 2] = (float)unfix(fz);
+    }
+}
+
+// --- Langevin BAOAB ---------------------------------------------------------------
+// Standard normals from Philox4x64-10 (key (seed, 0), counter (replica, step,
+// 4, atom)) by Box-Muller on (u1, u2) and (u3, u4), u1, u3 in (0, 1].
+__device__ __forceinline__ float3 md_normals(u64 seed, u64 r, u64 step, u64 atom) {
+    const Philox4 w = philox4x64(r, step, 4, atom, seed, 0);
+    const float u1 = (float)(((double)(w.w[0] >> 11) + 1.0) * (1.0 / 9007199254740992.0));
+    const float u2 = (float)unif53(w.w[1]);
+    const float u3 = (float)(((double)(w.w[2] >> 11) + 1.0) * (1.0 / 9007199254740992.0));
+    const float u4 = (float)unif53(w.w[3]);
+    const float m1 = sqrtf(-2.0f * logf(u1)), m2 = sqrtf(-2.0f * logf(u3));
+    float s2, c2, s4, c4;
+    sincospif(2.0f * u2, &s2, &c2);
+    sincospif(2.0f * u4, &s4, &c4);
+    return make_float3(m1 * c2, m1 * s2, m2 * c4);
+}
+
+// B (half kick), A (half drift), O (exact Ornstein-Uhlenbeck), A (half drift)
+__global__ void k_md_first(AtomArgs A, MDArgs m, int step_in_block) {
+    const int r = blockIdx.y;
+    const int64_t base = A.atom_off[r];
+    const int n = (int)(A.atom_off[r + 1] - base);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t g = base + i;
+    const u64 step = m.ctr[0] + (u64)step_in_block + 1;
+    float4 x = m.xyzq[g], v = m.vel[g];
+    const float4 f = m.force[g];
+    const float3 z = md_normals(m.seed, (u64)r, step, (u64)i);
+    v.x = fmaf(m.h * m.inv_m, f.x, v.x);
+    v.y = fmaf(m.h * m.inv_m, f.y, v.y);
+    v.z = fmaf(m.h * m.inv_m, f.z, v.z);
+    x.x = fmaf(m.h, v.x, x.x); x.y = fmaf(m.h, v.y, x.y); x.z = fmaf(m.h, v.z, x.z);
+    v.x = fmaf(m.c1, v.x, m.c2 * z.x);
+    v.y = fmaf(m.c1, v.y, m.c2 * z.y);
+    v.z = fmaf(m.c1, v.z, m.c2 * z.z);
+    x.x = fmaf(m.h, v.x, x.x); x.y = fmaf(m.h, v.y, x.y); x.z = fmaf(m.h, v.z, x.z);
+    m.xyzq[g] = x;
+    m.vel[g] = v;
+}
+
+// Total force (pair accumulators + chain bonds k (r - r0)^2) then the closing
+// half kick B; kick == 0 only stores the force (start of a trajectory).
+__global__ void k_md_second(AtomArgs A, MDArgs m, int kick) {
+    const int r = blockIdx.y;
+    const int64_t base = A.atom_off[r];
+    const int n = (int)(A.atom_off[r + 1] - base);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t g = base + i;
+    float fx = (float)unfix(A.F_acc[g]);
+    float fy = (float)unfix(A.F_acc[A.N + g]);
+    float fz = (float)unfix(A.F_acc[2 * A.N + g]);
+    A.F_acc[g] = 0;
+    A.F_acc[A.N + g] = 0;
+    A.F_acc[2 * A.N + g] = 0;
+    const float4 xi = m.xyzq[g];
+    if (m.bond_k != 0.0f) {
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const int j = side ? i + 1 : i - 1;
+            if (j < 0 || j >= n) continue;
+            const float4 xj = m.xyzq[base + j];
+            const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+            const float rr = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+            // dE/dr = 2 k (r - r0); force on i points along +d when stretched
+            const float s = 2.0f * m.bond_k * (rr - m.bond_r0) / rr;
+            fx = fmaf(s, dx, fx); fy = fmaf(s, dy, fy); fz = fmaf(s, dz, fz);
+        }
+    }
+    m.force[g] = make_float4(fx, fy, fz, 0.0f);
+    if (kick) {
+        float4 v = m.vel[g];
+        v.x = fmaf(m.h * m.inv_m, fx, v.x);
+        v.y = fmaf(m.h * m.inv_m, fy, v.y);
+        v.z = fmaf(m.h * m.inv_m, fz, v.z);
+        m.vel[g] = v;
+    }
+}
+
+__global__ void k_set_counters(u64* ctr, u64 step, u64 attempt) {
+    ctr[0] = step;
+    ctr[1] = attempt;
+}
+
+__global__ void k_advance_counters(u64* ctr, u64 steps, u64 attempts) {
+    ctr[0] += steps;
+    ctr[1] += attempts;
+}
+
+// --- Monte Carlo state change at fixed Born radii (Eq. 8, Eq. 9) -------------------
+// One block per replica.  The energy change of a site's charge change dq is
+//   dE = sum_k dq_k phi_k + 1/2 sum_{k,l} dq_k dq_l A_kl
+// exactly (E is quadratic in q at fixed R), with the site rows
+//   phi_k = sum_{j != k} q_j (k_c / r_kj - tau k_e / f_kj) - tau k_e q_k / R_k
+// and the site-site block A_kl = k_c / r_kl - tau k_e / f_kl (k != l),
+// A_kk = -tau k_e / R_k.  Terms in FP32, sums and the decision in FP64.
+constexpr int MC_MAX_SITE_ATOMS = 128;
+
+__device__ __forceinline__ float mc_R(const MCArgs& A, int64_t g) {
+    return A.R ? A.R[g] : A.Rh[g].x;
+}
+
+__global__ void __launch_bounds__(256) k_mc(MCArgs A) {
+    __shared__ int s_site, s_new, s_cur;
+    __shared__ u64 s_w2;
+    __shared__ double s_phi[MC_MAX_SITE_ATOMS];
+    __shared__ double s_dq[MC_MAX_SITE_ATOMS];
+    __shared__ double sh[32];
+    __shared__ int s_acc;
+    const int r = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const int64_t base = A.atom_off[r];
+    const int n = (int)(A.atom_off[r + 1] - base);
+    if (tid == 0) {
+        const u64 step = (A.ctr ? A.ctr[0] : 0) + A.step;
+        const Philox4 w = philox4x64((u64)r, step, 1 + (u64)A.kind, 0, A.seed, 0);
+        int n_kind = 0;
+        for (int s = A.site_off[r]; s < A.site_off[r + 1]; ++s) n_kind += (A.site_kind[s] == A.kind);
+        s_site = -1;
+        if (n_kind > 0) {
+            const int want = pick_int(w.w[0], n_kind);
+            for (int s = A.site_off[r], c = 0; s < A.site_off[r + 1]; ++s)
+                if (A.site_kind[s] == A.kind) {
+                    if (c == want) { s_site = s; break; }
+                    ++c;
+                }
+            const int cur = A.state[s_site];
+            const int k = pick_int(w.w[1], A.site_nstates[s_site] - 1);
+            s_cur = cur;
+            s_new = (k < cur) ? k : k + 1;
+            s_w2 = w.w[2];
+        }
+    }
+    __syncthreads();
+    const int site = s_site;
+    if (site < 0) {
+        if (tid == 0) {
+            if (A.dG_out) A.dG_out[r] = 0.0;
+            if (A.acc_out) A.acc_out[r] = 0;
+        }
+        return;
+    }
+    const int a0 = A.site_atom_off[site];
+    const int na = A.site_atom_off[site + 1] - a0;
+    if (na > MC_MAX_SITE_ATOMS || na < 0) {   // rejected on the host; never index past the buffers
+        if (tid == 0) {
+            if (A.dG_out) A.dG_out[r] = __longlong_as_double(0x7ff8000000000000LL);
+            if (A.acc_out) A.acc_out[r] = 0;
+        }
+        return;
+    }
+    const int qo = A.site_q_off[site] + s_new * na;
+    for (int k = tid; k < na; k += blockDim.x) {
+        const int64_t gk = base + A.site_atom_idx[a0 + k];
+        s_dq[k] = (double)A.q_state[qo + k] - (double)A.xyzq[gk].w;
+    }
+    const float tke = (float)A.tau_ke, kc = (float)A.kc;
+    // site rows: warp w handles site atoms k = w, w + nw, ...
+    for (int k = wid; k < na; k += nw) {
+        const int lk = A.site_atom_idx[a0 + k];
+        const int64_t gk = base + lk;
+        const float4 xk = A.xyzq[gk];
+        const float Rk = mc_R(A, gk);
+        double acc = 0.0;
+        for (int j = lane; j < n; j += 32) {
+            const int64_t gj = base + j;
+            const float4 xj = A.xyzq[gj];
+            float term;
+            if (j == lk) {
+                term = -tke * xj.w / Rk;
+            } else {
+                const float dx = xj.x - xk.x, dy = xj.y - xk.y, dz = xj.z - xk.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const float Rj = mc_R(A, gj);
+                const float RR = Rk * Rj;
+                const float f2 = fmaf(RR, __expf(-r2 / (4.0f * RR)), r2);
+                term = xj.w * (kc * rsqrtf(r2) - tke * rsqrtf(f2));
+            }
+            acc += (double)term;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) s_phi[k] = acc;
+    }
+    __syncthreads();
+    // linear term + site-site block, FP64
+    double part = 0.0;
+    for (int t = tid; t < na * na; t += blockDim.x) {
+        const int k = t / na, l = t % na;
+        const int64_t gk = base + A.site_atom_idx[a0 + k];
+        double Akl;
+        if (k == l) {
+            Akl = -A.tau_ke / (double)mc_R(A, gk);
+            part += s_dq[k] * s_phi[k];
+        } else {
+            const int64_t gl = base + A.site_atom_idx[a0 + l];
+            const float4 xk = A.xyzq[gk], xl = A.xyzq[gl];
+            const double dx = (double)xl.x - xk.x, dy = (double)xl.y - xk.y, dz = (double)xl.z - xk.z;
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            const double RR = (double)mc_R(A, gk) * (double)mc_R(A, gl);
+            const double f = sqrt(r2 + RR * exp(-r2 / (4.0 * RR)));
+            Akl = A.kc / sqrt(r2) - A.tau_ke / f;
+        }
+        part += 0.5 * s_dq[k] * s_dq[l] * Akl;
+    }
+    const double dE = block_sum_d(part, sh);
+    if (tid == 0) {
+        const int so = A.site_state_off[site];
+        const int cur = s_cur, nxt = s_new;
+        double dG = dE - (A.G_ref[so + nxt] - A.G_ref[so + cur]);
+        dG += FARADAY * (A.E[r] - A.E0_ref[site]) * (double)(A.n_e[so + nxt] - A.n_e[so + cur]);
+        dG += A.kT * LN10 * (A.pH[r] - A.pKa_ref[site]) * (double)(A.n_H[so + nxt] - A.n_H[so + cur]);
+        const double u = unif53(s_w2);
+        const int acc = (dG <= 0.0) || (u < exp(-dG / A.kT));
+        if (A.dG_out) A.dG_out[r] = dG;
+        if (A.acc_out) A.acc_out[r] = (uint8_t)acc;
+        if (acc) A.state[site] = nxt;
+        s_acc = acc;
+    }
+    __syncthreads();
+    if (s_acc)
+        for (int k = tid; k < na; k += blockDim.x) {
+            const int64_t gk = base + A.site_atom_idx[a0 + k];
+            A.xyzq[gk].w = A.q_state[qo + k];
+        }
+}
+
+// --- replica exchange (Eq. 14, 15; schedule of Sec. III.B) ----------------------------
+__device__ __forceinline__ void exchange_pair(int32_t* rep_at_slot, const double* values,
+                                              const int32_t* n_count, double c, int l, int len,
+                                              int ladder_stride, int slot_stride, int a, int b,
+                                              u64 attempt, u64 seed, double* value_of_rep,
+                                              double* delta_out, uint8_t* acc_out) {
+    int32_t* pa = &rep_at_slot[l * ladder_stride + a * slot_stride];
+    int32_t* pb = &rep_at_slot[l * ladder_stride + b * slot_stride];
+    const int i = *pa, j = *pb;
+    const double delta = c * (values[b] - values[a]) * (double)(n_count[i] - n_count[j]);
+    const Philox4 w = philox4x64((u64)(l * len + a), attempt, 3, 0, seed, 0);
+    const double u = unif53(w.w[0]);
+    const int acc = (delta <= 0.0) || (u < exp(-delta));
+    if (delta_out) delta_out[l * len + a] = delta;
+    if (acc_out) acc_out[l * len + a] = (uint8_t)acc;
+    if (acc) { *pa = j; *pb = i; }
+    if (value_of_rep) {
+        value_of_rep[*pa] = values[a];
+        value_of_rep[*pb] = values[b];
+    }
+}
+
+// the partner of slot a in attempt `attempt`, or -1
+__device__ __forceinline__ int partner(int a, int len, u64 attempt, int wrap) {
+    if ((a & 1) != (int)(attempt & 1)) return -1;
+    int b = a + 1;
+    if (b == len) {
+        if (!(wrap && (attempt & 1) && (len % 2 == 0))) return -1;
+        b = 0;
+    }
+    return b;
+}
+
+__global__ void k_exchange(ExArgs A) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= A.n_ladders * A.len) return;
+    const int l = t / A.len, a = t % A.len;
+    const u64 attempt = (A.ctr ? A.ctr[1] : 0) + A.attempt;
+    if (A.delta_out) A.delta_out[t] = __longlong_as_double(0x7ff8000000000000LL);
+    if (A.acc_out) A.acc_out[t] = 0;
+    const int b = partner(a, A.len, attempt, A.wrap);
+    if (b < 0) return;
+    const double c = (A.dim == 0) ? FARADAY / A.kT : LN10;
+    exchange_pair(A.rep_at_slot, A.values, A.n_count, c, l, A.len, A.ladder_stride, A.slot_stride,
+                  a, b, attempt, A.seed, A.value_of_rep, A.delta_out, A.acc_out);
+}
+
+__device__ __forceinline__ int bound_count(const GridExArgs& A, int rep, int kind) {
+    int c = 0;
+    for (int s = A.site_off[rep]; s < A.site_off[rep + 1]; ++s) {
+        if (A.site_kind[s] != kind) continue;
+        const int so = A.site_state_off[s] + A.state[s];
+        c += kind ? A.n_e[so] : A.n_H[so];
+    }
+    return c;
+}
+
+__global__ void k_grid_exchange(GridExArgs A) {
+    const u64 attempt = A.ctr[1];
+    const int dimE = (A.ex_dim == 0) || (A.ex_dim == 2 && ((attempt >> 1) & 1) == 0);
+    const int n_lad = dimE ? A.n_pH : A.n_E;
+    const int len = dimE ? A.n_E : A.n_pH;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_lad * len) return;
+    const int l = t / len, a = t % len;
+    const int b = partner(a, len, attempt, A.wrap);
+    if (b < 0) return;
+    const int ladder_stride = dimE ? A.n_E : 1;
+    const int slot_stride = dimE ? 1 : A.n_E;
+    int32_t* pa = &A.grid[l * ladder_stride + a * slot_stride];
+    int32_t* pb = &A.grid[l * ladder_stride + b * slot_stride];
+    const int i = *pa, j = *pb;
+    const int kind = dimE ? 1 : 0;
+    const double* values = dimE ? A.E_ladder : A.pH_ladder;
+    const double c = dimE ? FARADAY / A.kT : LN10;
+    const double delta = c * (values[b] - values[a]) * (double)(bound_count(A, i, kind) - bound_count(A, j, kind));
+    const Philox4 w = philox4x64((u64)(l * len + a), attempt, 3, 0, A.seed, 0);
+    const int acc = (delta <= 0.0) || (unif53(w.w[0]) < exp(-delta));
+    if (acc) { *pa = j; *pb = i; }
+    double* vr = dimE ? A.E_rep : A.pH_rep;
+    vr[*pa] = values[a];
+    vr[*pb] = values[b];
+}
+
+__global__ void k_count(const int32_t* site_off, const int32_t* site_kind, const int32_t* site_state_off,
+                        const int32_t* n_H, const int32_t* n_e, const int32_t* state, int32_t kind,
+                        int32_t M, int32_t* out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= M) return;
+    int c = 0;
+    for (int s = site_off[r]; s < site_off[r + 1]; ++s) {
+        if (site_kind[s] != kind) continue;
+        const int so = site_state_off[s] + state[s];
+        c += kind ? n_e[so] : n_H[so];
+    }
+    out[r] = c;
+}
+
+// --- launchers -----------------------------------------------------------------------
+static dim3 atom_grid(const AtomArgs& a) {
+    return dim3((unsigned)((a.max_n + 255) / 256 > 0 ? (a.max_n + 255) / 256 : 1), (unsigned)a.M);
+}
+
+cudaError_t launch_born_finalize(const AtomArgs& a, float* R_out, cudaStream_t s) {
+    k_born_finalize<<<atom_grid(a), 256, 0, s>>>(a, R_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy_finalize(const AtomArgs& a, int want_energy, double* phi_out, cudaStream_t s) {
+    k_energy_finalize<<<atom_grid(a), 256, 0, s>>>(a, want_energy, phi_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forces_out(const AtomArgs& a, int64_t* F_fixed, float* F_out, double* E_out,
+                              cudaStream_t s) {
+    k_forces_out<<<atom_grid(a), 256, 0, s>>>(a, F_fixed, F_out, E_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_md_first(const AtomArgs& a, const MDArgs& m, int step_in_block, cudaStream_t s) {
+    k_md_first<<<atom_grid(a), 256, 0, s>>>(a, m, step_in_block);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_md_second(const AtomArgs& a, const MDArgs& m, cudaStream_t s) {
+    k_md_second<<<atom_grid(a), 256, 0, s>>>(a, m, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_md_force_only(const AtomArgs& a, const MDArgs& m, cudaStream_t s) {
+    k_md_second<<<atom_grid(a), 256, 0, s>>>(a, m, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_counters(u64* ctr, u64 step, u64 attempt, cudaStream_t s) {
+    k_set_counters<<<1, 1, 0, s>>>(ctr, step, attempt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_advance_counters(u64* ctr, u64 steps, u64 attempts, cudaStream_t s) {
+    k_advance_counters<<<1, 1, 0, s>>>(ctr, steps, attempts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mc(const MCArgs& a, int32_t M, cudaStream_t s) {
+    if (M == 0) return cudaSuccess;
+    k_mc<<<M, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_exchange(const ExArgs& a, cudaStream_t s) {
+    const int n = a.n_ladders * a.len;
+    if (n == 0) return cudaSuccess;
+    k_exchange<<<(n + 255) / 256, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grid_exchange(const GridExArgs& a, cudaStream_t s) {
+    const int n = a.n_pH * a.n_E;
+    if (n < 2) return cudaSuccess;
+    k_grid_exchange<<<(n + 255) / 256, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count(const int32_t* site_off, const int32_t* site_kind,
+                         const int32_t* site_state_off, const int32_t* n_H, const int32_t* n_e,
+                         const int32_t* state, int32_t kind, int32_t M, int32_t* out,
+                         cudaStream_t s) {
+    if (M == 0) return cudaSuccess;
+    k_count<<<(M + 127) / 128, 128, 0, s>>>(site_off, site_kind, site_state_off, n_H, n_e, state,
+                                            kind, M, out);
+    return cudaGetLastError();
+}
+
+}  // namespace gbk

@@ -1,0 +1,69 @@
+// Device helpers shared by the GB300 kernels: constants, fixed-point
+// accumulation, ghost atoms for ragged tails, Philox4x64-10.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gbremd.h"
+
+namespace gbk {
+
+// Coulomb constant (kcal A / (mol e^2)), Faraday constant (kcal / (mol V)).
+constexpr double KE = 332.0522173;
+constexpr double FARADAY = 23.0605478;
+constexpr double LN10 = 2.302585092994045684;
+// (kcal/mol/A) / amu -> A / ps^2
+constexpr double ACCEL = 418.4;
+
+// Fixed-point scales: forces, dE/dR, dE/dq and energies carry 32 fractional
+// bits; Born integrals (values below ~10 / A) carry 40.
+constexpr float FIX = 4294967296.0f;
+constexpr double FIX_INV = 1.0 / 4294967296.0;
+constexpr float FIX_I = 1099511627776.0f;
+constexpr double FIX_I_INV = 1.0 / 1099511627776.0;
+
+typedef unsigned long long u64;
+
+__device__ __forceinline__ long long fix(float v) { return __float2ll_rn(v * FIX); }
+__device__ __forceinline__ long long fix_i(float v) { return __float2ll_rn(v * FIX_I); }
+__device__ __forceinline__ long long fix_d(double v) { return __double2ll_rn(v * 4294967296.0); }
+__device__ __forceinline__ void red_add(u64* p, long long v) {
+    atomicAdd(p, (u64)v);
+}
+__device__ __forceinline__ double unfix(u64 v) { return (double)(long long)v * FIX_INV; }
+
+// Lanes past the end of a replica hold "ghost" atoms: zero charge, zero
+// descreening radius, zero chain factor, parked far away at distinct spots.
+// Every term a ghost contributes to a real atom is then exactly +-0.
+__device__ __forceinline__ float ghost_x(int local) { return 1.0e7f + 16.0f * (float)local; }
+
+__device__ __forceinline__ float shfl(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+
+// Philox4x64-10 (Salmon et al., SC'11): 10 rounds of two 64x64->128 multiplies
+// with the published multipliers, key bumped by the published Weyl constants.
+struct Philox4 {
+    u64 w[4];
+};
+
+__device__ __forceinline__ Philox4 philox4x64(u64 c0, u64 c1, u64 c2, u64 c3, u64 k0, u64 k1) {
+    const u64 M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        u64 hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+        u64 hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+        u64 n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += 0x9E3779B97F4A7C15ULL;
+        k1 += 0xBB67AE8584CAA73BULL;
+    }
+    Philox4 r;
+    r.w[0] = c0; r.w[1] = c1; r.w[2] = c2; r.w[3] = c3;
+    return r;
+}
+
+// u in [0, 1) from the top 53 bits; integer in [0, n) from the top 32 bits.
+__device__ __forceinline__ double unif53(u64 w) { return (double)(w >> 11) * (1.0 / 9007199254740992.0); }
+__device__ __forceinline__ int pick_int(u64 w, int n) { return (int)(((w >> 32) * (u64)n) >> 32); }
+
+}  // namespace gbk

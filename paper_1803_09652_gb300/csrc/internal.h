@@ -1,0 +1,173 @@
+// Internal interfaces between the host library and the kernel translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gbremd.h"
+
+namespace gbk {
+
+typedef unsigned long long u64;
+
+// Everything the O(N^2) pair passes read and write.
+struct PairArgs {
+    const int64_t* atom_off;   // [M+1]
+    const float4* xyzq;        // x, y, z, q
+    const float2* rad;         // rho, S
+    const float2* Rh;          // R, 1/(2R)          (pass 2)
+    const float* cc;           // chain factor c_i   (pass 3)
+    float offset;
+    float tau_ke;              // (1/eps_in - 1/eps_out) k_e
+    float kc;                  // k_e / eps_in
+    float rep_k, rep_sigma;    // soft repulsion (rep_k == 0: off)
+    u64* I_acc;                // [N]   Born integrals, 2^40 fixed point
+    u64* dR_acc;               // [N]   dE/dR pair part, 2^32
+    u64* phi_acc;              // [N]   dE/dq pair part, 2^32
+    u64* F_acc;                // [3N]  forces x | y | z, 2^32
+    u64* E_acc;                // [M*4] E_GB, E_Coul, E_rep, spare, 2^32
+    int64_t N;
+};
+
+// One warp task: replica, first (I, J) 32-atom tile pair, number of tile pairs.
+// Tile pairs of a replica are walked row by row over the upper triangle I <= J.
+struct TaskList {
+    int4* d_tasks = nullptr;
+    int n_tasks = 0;
+};
+
+enum PassKind { PASS_BORN = 0, PASS_ENERGY = 1, PASS_CHAIN = 2 };
+
+// flags for the energy pass
+enum { EF_ENERGY = 1, EF_PHI = 2, EF_REP = 4 };
+
+cudaError_t launch_pairs(int pass, int flags, const PairArgs& a, const TaskList& t,
+                         int warps_per_block, cudaStream_t s);
+
+// O(N) kernels --------------------------------------------------------------
+
+struct AtomArgs {
+    const int64_t* atom_off;
+    int32_t M;
+    int32_t max_n;             // largest replica
+    const float4* xyzq;
+    const float2* rad;
+    float alpha, beta, gamma, offset;
+    double tau_ke;
+    u64* I_acc;
+    u64* dR_acc;
+    u64* phi_acc;
+    u64* F_acc;
+    u64* E_acc;
+    float2* Rh;
+    float* cfac;               // a_i dR_i/dpsi_i
+    float* cc;                 // c_i = dE/dR_i * cfac_i
+    int* err;
+    int64_t N;
+};
+
+cudaError_t launch_born_finalize(const AtomArgs& a, float* R_out, cudaStream_t s);
+cudaError_t launch_energy_finalize(const AtomArgs& a, int want_energy, double* phi_out,
+                                   cudaStream_t s);
+cudaError_t launch_forces_out(const AtomArgs& a, int64_t* F_fixed, float* F_out, double* E_out,
+                              cudaStream_t s);
+
+struct MDArgs {
+    float4* xyzq;
+    float4* vel;
+    float4* force;
+    const u64* ctr;            // [0] step base, [1] exchange attempt base
+    float h;                   // dt / 2
+    float inv_m;               // ACCEL / mass
+    float c1, c2;              // exp(-gamma dt), sqrt((1 - c1^2) kT ACCEL / m)
+    float bond_k, bond_r0;
+    u64 seed;
+};
+
+cudaError_t launch_md_first(const AtomArgs& a, const MDArgs& m, int step_in_block, cudaStream_t s);
+cudaError_t launch_md_second(const AtomArgs& a, const MDArgs& m, cudaStream_t s);
+cudaError_t launch_md_force_only(const AtomArgs& a, const MDArgs& m, cudaStream_t s);
+cudaError_t launch_set_counters(u64* ctr, u64 step, u64 attempt, cudaStream_t s);
+cudaError_t launch_advance_counters(u64* ctr, u64 steps, u64 attempts, cudaStream_t s);
+
+struct MCArgs {
+    const int64_t* atom_off;
+    const int32_t* site_off;
+    const int32_t* site_kind;
+    const int32_t* site_nstates;
+    const int32_t* site_atom_off;
+    const int32_t* site_atom_idx;
+    const int32_t* site_state_off;
+    const int32_t* site_q_off;
+    const float* q_state;
+    const double* G_ref;
+    const int32_t* n_H;
+    const int32_t* n_e;
+    const double* pKa_ref;
+    const double* E0_ref;
+    float4* xyzq;
+    const float* R;            // Born radii (stride 1) ...
+    const float2* Rh;          // ... or (R, 1/(2R)) pairs when R == nullptr
+    const double* pH;
+    const double* E;
+    double kT;
+    double tau_ke, kc;
+    u64 seed;
+    u64 step;
+    const u64* ctr;            // when non-null the step is ctr[0] + step
+    int32_t kind;
+    int32_t* state;
+    double* dG_out;
+    uint8_t* acc_out;
+};
+
+cudaError_t launch_mc(const MCArgs& a, int32_t M, cudaStream_t s);
+
+struct ExArgs {
+    int32_t n_ladders, len, ladder_stride, slot_stride;
+    const double* values;
+    int32_t* rep_at_slot;
+    const int32_t* n_count;
+    int32_t dim;
+    u64 attempt;
+    const u64* ctr;            // when non-null the attempt is ctr[1] + attempt
+    u64 seed;
+    double kT;
+    int32_t wrap;
+    double* value_of_rep;
+    double* delta_out;
+    uint8_t* acc_out;
+};
+
+cudaError_t launch_exchange(const ExArgs& a, cudaStream_t s);
+
+// Two-dimensional grid exchange used by the MD driver: the dimension of
+// attempt k is E when (k / 2) is even and pH otherwise (or fixed by ex_dim).
+struct GridExArgs {
+    int32_t n_pH, n_E;
+    const double* E_ladder;
+    const double* pH_ladder;
+    int32_t* grid;
+    const int32_t* site_off;
+    const int32_t* site_kind;
+    const int32_t* site_state_off;
+    const int32_t* n_H;
+    const int32_t* n_e;
+    const int32_t* state;
+    const u64* ctr;
+    int32_t ex_dim;            // 0 E only, 1 pH only, 2 alternate
+    int32_t wrap;
+    u64 seed;
+    double kT;
+    double* E_rep;
+    double* pH_rep;
+};
+
+cudaError_t launch_grid_exchange(const GridExArgs& a, cudaStream_t s);
+
+cudaError_t launch_count(const int32_t* site_off, const int32_t* site_kind,
+                         const int32_t* site_state_off, const int32_t* n_H,
+                         const int32_t* n_e, const int32_t* state, int32_t kind, int32_t M,
+                         int32_t* out, cudaStream_t s);
+
+}  // namespace gbk

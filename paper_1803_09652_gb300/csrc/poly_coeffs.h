@@ -1,0 +1,13 @@
+/* Generated by gen_poly.py: far-field HCT polynomials, see that script. */
+#pragma once
+#define GB_POLY_YMAX 0.36000000f
+/* g(y), degree 8, max relative error in FP32 Horner 1.23e-07 */
+#define GB_POLY_G_DEG 8
+__device__ __forceinline__ float gb_poly_g(float y) {
+    return fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(6.372991085e+00f, y, -3.979435205e+00f), y, 3.000669241e+00f), y, 4.458978176e-01f), y, 9.718360901e-01f), y, 8.843408227e-01f), y, 8.573058248e-01f), y, 7.999977469e-01f), y, 6.666666865e-01f);
+}
+/* h(y), degree 10, max relative error in FP32 Horner 1.47e-07 */
+#define GB_POLY_H_DEG 10
+__device__ __forceinline__ float gb_poly_h(float y) {
+    return fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(2.890447998e+02f, y, -3.036016235e+02f), y, 2.056483459e+02f), y, -4.527267456e+01f), y, 2.778405762e+01f), y, 1.125458431e+01f), y, 1.104221439e+01f), y, 8.882757187e+00f), y, 6.857286453e+00f), y, 4.799998760e+00f), y, 2.666666746e+00f);
+}

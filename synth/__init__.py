@@ -171,6 +171,8 @@ def compact_chain(n: int, seed: int, step: float = 1.5, clash: float = 1.2,
     `density`.  After 1000 rejected proposals the walk backs up one atom.
     Returns float32 [n, 3].
     """
+    if n <= 0:
+        return np.zeros((0, 3), dtype=np.float32)
     rng = np.random.default_rng(seed)
     r_sph = (3.0 * n / (4.0 * math.pi * density)) ** (1.0 / 3.0)
     cell = step + clash
@@ -268,7 +270,8 @@ def make_replica(n: int, seed: int, site_specs: List[tuple]) -> Replica:
     xyz = compact_chain(n, seed)
     rng = np.random.default_rng(seed + 1_000_003)
     q = rng.normal(0.0, 0.3, size=n)
-    q -= q.mean()
+    if n > 1:
+        q -= q.mean()
     q = q.astype(np.float32)
     rho = np.asarray(RADIUS_SET, dtype=np.float32)[rng.integers(0, len(RADIUS_SET), size=n)]
     screen = np.full(n, SCREEN, dtype=np.float32)

@@ -1,0 +1,117 @@
+"""GPU MD driver: one BAOAB step against the oracle on identical inputs (MD is
+chaotic, so parity is per step), graph replay against direct launches, and
+E-REMD bookkeeping over a longer segment."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_common import F_ABS, KT, device, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1803_09652_gb300 as p
+    return p
+
+
+def _setup(pkg, b, seed, mc_every=0, ex_every=0, with_sites=False):
+    import torch
+    dev = device()
+    params = pkg.default_params(rep_k=10.0, rep_sigma=2.5)
+    ctx = pkg.Context(b.atom_off, params)
+    N, M = b.n_atoms, b.n_rep
+    S = dict(xyzq=torch.as_tensor(b.xyzq(), device=dev),
+             rad=torch.as_tensor(b.rad_screen(), device=dev),
+             vel=torch.zeros((N, 4), dtype=torch.float32, device=dev),
+             force=torch.zeros((N, 4), dtype=torch.float32, device=dev),
+             R=torch.zeros(N, dtype=torch.float32, device=dev),
+             pH=torch.as_tensor(b.pH.copy(), device=dev), E=torch.as_tensor(b.E.copy(), device=dev),
+             grid=torch.arange(M, dtype=torch.int32, device=dev),
+             E_ladder=torch.as_tensor(synth.e_ladder(M), device=dev),
+             pH_ladder=torch.as_tensor(np.array([b.pH[0]]), device=dev))
+    sites = None
+    if with_sites:
+        t = b.site_tables(oracle.site_reference_energies(b, oracle_params()))
+        sites = pkg.SiteTables(t, M, dev)
+        S["state"] = torch.zeros(t["n_sites"], dtype=torch.int32, device=dev)
+    st = pkg.MDState()
+    for k in ("xyzq", "vel", "force", "R", "pH", "E", "grid", "E_ladder", "pH_ladder"):
+        setattr(st, k, S[k].data_ptr())
+    st.rad_screen = S["rad"].data_ptr()
+    st.state = S["state"].data_ptr() if with_sites else None
+    st.n_E, st.n_pH = M, 1
+    st.dt, st.friction, st.mass, st.kT = 0.002, 10.0, 12.0, KT
+    st.bond_k, st.bond_r0 = 300.0, 1.5
+    st.seed, st.step, st.attempt = seed, 0, 0
+    st.mc_every, st.ex_every, st.ex_dim, st.wrap = mc_every, ex_every, 0, 1
+    ctx.md_init(st)
+    return ctx, st, S, sites
+
+
+def test_one_baoab_step_matches_oracle(pkg):
+    import torch
+    b = synth.random_batch([120, 64, 33], seed=3, sites=False)
+    ctx, st, S, _ = _setup(pkg, b, seed=5)
+    torch.cuda.synchronize()
+    x, q, rho, scr, off = oracle.batch_arrays(b)
+    p = oracle_params(rep_k=10.0, rep_sigma=2.5)
+    F0, _ = oracle.forces_all(off, x, q, rho, scr, p)
+    assert np.abs(S["force"][:, :3].cpu().numpy() - F0).max() <= F_ABS
+    ctx.md_segment(st, None, 1)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    v = np.zeros_like(x)
+    oracle.md_step(off, x, v, q, rho, scr, F0, 5, 1, p)
+    assert np.abs(S["xyzq"][:, :3].cpu().numpy() - x).max() <= 1e-5
+    assert np.abs(S["vel"][:, :3].cpu().numpy() - v).max() <= 1e-4
+    assert np.abs(S["force"][:, :3].cpu().numpy() - F0).max() <= F_ABS
+    assert st.step == 1
+
+
+def test_graph_replay_equals_direct_launches(pkg):
+    import torch
+    b = synth.config_eremd(4, 300)
+    ctx1, st1, S1, sites1 = _setup(pkg, b, seed=8, mc_every=10, ex_every=50, with_sites=True)
+    ctx2, st2, S2, sites2 = _setup(pkg, b, seed=8, mc_every=10, ex_every=50, with_sites=True)
+    ctx1.md_segment(st1, sites1, 100)           # two captured blocks of 50
+    for _ in range(100):
+        ctx2.md_segment(st2, sites2, 1)         # direct launches
+    torch.cuda.synchronize()
+    ctx1.sync_status()
+    ctx2.sync_status()
+    for k in ("xyzq", "vel", "force", "state", "E", "grid"):
+        assert torch.equal(S1[k], S2[k]), k
+    assert st1.step == st2.step == 100 and st1.attempt == st2.attempt == 2
+
+
+def test_eremd_segment_bookkeeping(pkg):
+    import torch
+    b = synth.config_eremd(8, 256)
+    ctx, st, S, sites = _setup(pkg, b, seed=11, mc_every=10, ex_every=20, with_sites=True)
+    ctx.md_segment(st, sites, 400)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    grid = S["grid"].cpu().numpy()
+    assert sorted(grid.tolist()) == list(range(8))
+    E = S["E"].cpu().numpy()
+    lad = synth.e_ladder(8)
+    assert np.allclose(E[grid], lad)
+    x = S["xyzq"].cpu().numpy()
+    assert np.all(np.isfinite(x))
+    # charges always equal the site-state charges
+    t = sites.t
+    st_h = S["state"].cpu().numpy()
+    tables = b.site_tables()
+    for s in range(tables["n_sites"]):
+        r = np.searchsorted(tables["site_off"], s, side="right") - 1
+        a0, a1 = tables["site_atom_off"][s], tables["site_atom_off"][s + 1]
+        idx = tables["site_atom_idx"][a0:a1] + b.atom_off[r]
+        na = a1 - a0
+        qo = tables["site_q_off"][s] + st_h[s] * na
+        assert np.array_equal(x[idx, 3], tables["q_state"][qo:qo + na])
+    assert st.attempt == 20
