@@ -243,6 +243,34 @@ int gb_md_init(gb_ctx* ctx, gb_md_state* state, void* stream);
 int gb_md_segment(gb_ctx* ctx, gb_md_state* state, const gb_sites* sites, int64_t nsteps,
                   void* stream);
 
+/* Allocation-free energy / force evaluation of ONE molecule.
+ *
+ * The paper has no counterpart: this is a service for callers that cannot
+ * call cudaMalloc -- code whose device memory all belongs to an arena or pool
+ * allocator, plugins inside a host program that forbids allocations after
+ * start-up, real-time loops where an allocation could stall.  Such callers
+ * cannot create a gb_ctx, so this call keeps its workspace in a fixed array
+ * of device memory that the library declares statically (about 0.7 MB, held by
+ * every GPU that loads the library until the process exits).
+ *
+ * Same inputs, outputs and arithmetic as gb_energy_forces for a batch of one
+ * replica of n_atoms atoms (1 <= n_atoms <= GB_STATIC_MAX_ATOMS); E_out is
+ * double[3].  Works on the current device.  It allocates nothing: no
+ * cudaMalloc, no cudaFree, no allocating library routine.
+ *  - The first call on a device looks up the array's device address (once per
+ *    device); make that first call before any stream capture.
+ *  - Every call on a device shares the one array and clears its accumulators
+ *    first; calls that overlap on the GPU (other streams, other host threads)
+ *    race on it and must be serialised by the caller.
+ *  - Returns GB_ERR_INVALID_ARG when n_atoms is outside 1..GB_STATIC_MAX_ATOMS
+ *    or an argument is NULL / misaligned, GB_ERR_CUDA on a launch error.
+ *    Device-side non-finite results are not reported (there is no context to
+ *    hold the error word); they show up as NaN in the outputs. */
+#define GB_STATIC_MAX_ATOMS 8192
+int gb_energy_forces_static(int32_t n_atoms, const gb_params* params, const float* xyzq,
+                            const float* rad_screen, float* R_out, int64_t* F_fixed,
+                            float* F_out, double* E_out, double* dEdq_out, void* stream);
+
 /* Kernel timing inside the MD driver.  When enabled, CUDA events are recorded
  * around the three pair passes of every MD step (inside a captured graph they
  * become event nodes of the graph).  gb_pass_times waits for the events of the
