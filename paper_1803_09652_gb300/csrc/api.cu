@@ -29,6 +29,8 @@ struct gb_ctx {
     float* cfac = nullptr;
     float* cc = nullptr;
     int* err = nullptr;
+    double* mc_part = nullptr;          // MC site-row slice partials
+    int32_t mc_parts = 0;
     gbk::TaskList tasks;
     int wpb = 8;
     int tpt = 0;
@@ -87,18 +89,18 @@ cudaError_t zalloc(T** p, size_t n) {
     return cudaMemset(*p, 0, std::max<size_t>(n, 1) * sizeof(T));
 }
 
-// Cut the upper-triangle tile pairs of all replicas (row-major per replica,
-// replicas in order) into runs of `tpt` tile pairs, one warp task each.
+// Cut the work of all replicas (super-rows of 64 atoms against 32-atom tiles
+// J >= 2K, replicas in order) into runs of `tpt` tiles, one warp task each.
 int build_tasks(gb_ctx* c) {
     std::vector<int4> t;
     t.reserve((size_t)(c->total_tiles / c->tpt + 1));
     int64_t left_total = c->total_tiles;
-    int r = 0, I = 0, J = 0;
+    int r = 0, K = 0, J = 0;
     auto nb_of = [&](int rr) { return (int)((c->off_h[rr + 1] - c->off_h[rr] + 31) / 32); };
     while (r < c->M && nb_of(r) == 0) ++r;
     while (left_total > 0) {
         const int cnt = (int)std::min<int64_t>(c->tpt, left_total);
-        t.push_back(make_int4(r, I, J, cnt));
+        t.push_back(make_int4(r, K, J, cnt));
         left_total -= cnt;
         int64_t k = cnt;
         while (k > 0 && r < c->M) {
@@ -109,14 +111,13 @@ int build_tasks(gb_ctx* c) {
                 k = 0;
             } else {
                 k -= rowleft;
-                ++I;
-                J = I;
-                if (I == nb) {
+                ++K;
+                if (K == (nb + 1) / 2) {
                     ++r;
                     while (r < c->M && nb_of(r) == 0) ++r;
-                    I = 0;
-                    J = 0;
+                    K = 0;
                 }
+                J = 2 * K;
             }
         }
     }
@@ -256,8 +257,7 @@ extern "C" int gb_ctx_create(gb_ctx** out, int32_t n_rep, const int64_t* atom_of
     for (int r = 0; r < n_rep; ++r) {
         const int64_t n = atom_off[r + 1] - atom_off[r];
         c->max_n = (int32_t)std::max<int64_t>(c->max_n, n);
-        const int64_t nb = (n + 31) / 32;
-        c->total_tiles += nb * (nb + 1) / 2;
+        c->total_tiles += gbk::pair_units(n);
     }
     const size_t N = (size_t)c->N;
     cudaError_t e = cudaSuccess;
@@ -274,6 +274,8 @@ extern "C" int gb_ctx_create(gb_ctx** out, int32_t n_rep, const int64_t* atom_of
     step(zalloc(&c->cfac, N));
     step(zalloc(&c->cc, N));
     step(zalloc(&c->err, 1));
+    c->mc_parts = (c->max_n + gbk::MC_CHUNK - 1) / gbk::MC_CHUNK;
+    step(zalloc(&c->mc_part, (size_t)n_rep * std::max(c->mc_parts, 1) * gbk::MC_MAX_SITE_ATOMS));
     step(cudaStreamCreateWithFlags(&c->cs, cudaStreamNonBlocking));
     step(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
     step(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
@@ -311,6 +313,7 @@ extern "C" int gb_ctx_destroy(gb_ctx* c) {
     cudaFree(c->cfac);
     cudaFree(c->cc);
     cudaFree(c->err);
+    cudaFree(c->mc_part);
     if (c->cs) cudaStreamDestroy(c->cs);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
@@ -435,6 +438,8 @@ extern "C" int redox_ph_mc_step(gb_ctx* c, const gb_sites* sites, float* xyzq, c
     a.state = state;
     a.dG_out = dG_out;
     a.acc_out = acc_out;
+    a.phi_part = c->mc_part;
+    a.n_parts = c->mc_parts;
     GB_CHECK(c, gbk::launch_mc(a, c->M, (cudaStream_t)stream));
     return GB_OK;
 }
@@ -565,6 +570,8 @@ int enqueue_steps(gb_ctx* c, gb_md_state* st, const gb_sites* sites, int64_t len
                 a.state = st->state;
                 a.dG_out = nullptr;
                 a.acc_out = nullptr;
+                a.phi_part = c->mc_part;
+                a.n_parts = c->mc_parts;
                 GB_CHECK(c, gbk::launch_mc(a, c->M, s));
             }
         }

@@ -23,7 +23,11 @@ __device__ __forceinline__ double block_sum_d(double v, double* sh) {
 
 __device__ __forceinline__ void set_err(int* err, int code) { atomicCAS(err, 0, code); }
 
-// --- Born radii: I -> psi -> R (OBC), FP64 ------------------------------------
+// --- Born radii: I -> psi -> R (OBC) -------------------------------------------
+// R = 1 / (1/a - tanh(Phi)/rho), Phi = alpha psi - beta psi^2 + gamma psi^3.
+// Written without cancellation: with t = exp(-2|Phi|) and d = rho - a (exact
+// in FP32), 1/a - tanh(Phi)/rho = (d (1 + t) + 2 a t) / (a rho (1 + t)) for
+// Phi >= 0, and 1 - tanh^2 = 4 t / (1 + t)^2.  The integral is read in FP64.
 __global__ void k_born_finalize(AtomArgs A, float* R_out) {
     const int r = blockIdx.y;
     const int64_t base = A.atom_off[r];
@@ -31,20 +35,28 @@ __global__ void k_born_finalize(AtomArgs A, float* R_out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t g = base + i;
-    const double I = (double)(long long)A.I_acc[g] * FIX_I_INV;
+    const float I = (float)((double)(long long)A.I_acc[g] * FIX_I_INV);
     A.I_acc[g] = 0;
     const float2 rs = A.rad[g];
-    const double rho = rs.x;
-    const double a = rho - (double)A.offset;
-    const double psi = a * I;
-    const double al = A.alpha, be = A.beta, ga = A.gamma;
-    const double th = tanh(psi * (al + psi * (-be + ga * psi)));
-    const double R = 1.0 / (1.0 / a - th / rho);
-    const double dRdpsi = R * R * (1.0 - th * th) * (al - 2.0 * be * psi + 3.0 * ga * psi * psi) / rho;
-    if (!(R > 0.0) || !isfinite(R) || !isfinite(dRdpsi)) set_err(A.err, GB_ERR_NONFINITE);
-    A.Rh[g] = make_float2((float)R, (float)(0.5 / R));
-    A.cfac[g] = (float)(dRdpsi * a);
-    if (R_out) R_out[g] = (float)R;
+    const float rho = rs.x;
+    const float a = rho - A.offset;
+    const float d = rho - a;
+    const float psi = a * I;
+    const float Phi = psi * fmaf(psi, fmaf(A.gamma, psi, -A.beta), A.alpha);
+    const float t = __expf(-2.0f * fabsf(Phi));
+    const float onet = 1.0f + t;
+    float R;
+    if (Phi >= 0.0f) {
+        R = (a * rho * onet) / fmaf(d, onet, 2.0f * a * t);
+    } else {  // tanh < 0: 1/a + |tanh|/rho, no cancellation either
+        R = 1.0f / (1.0f / a + (1.0f - t) / (onet * rho));
+    }
+    const float sech2 = 4.0f * t / (onet * onet);
+    const float dRdpsi = R * R * sech2 * fmaf(psi, fmaf(3.0f * A.gamma, psi, -2.0f * A.beta), A.alpha) / rho;
+    if (!(R > 0.0f) || !isfinite(R) || !isfinite(dRdpsi)) set_err(A.err, GB_ERR_NONFINITE);
+    A.Rh[g] = make_float2(R, 0.5f / R);
+    A.cfac[g] = dRdpsi * a;
+    if (R_out) R_out[g] = R;
 }
 
 // --- self terms, dE/dR -> chain factor, dE/dq readout ----------------------------
@@ -193,129 +205,155 @@ __global__ void k_advance_counters(u64* ctr, u64 steps, u64 attempts) {
 }
 
 // --- Monte Carlo state change at fixed Born radii (Eq. 8, Eq. 9) -------------------
-// One block per replica.  The energy change of a site's charge change dq is
+// The energy change of a site's charge change dq is, exactly (E is quadratic
+// in q at fixed R),
 //   dE = sum_k dq_k phi_k + 1/2 sum_{k,l} dq_k dq_l A_kl
-// exactly (E is quadratic in q at fixed R), with the site rows
+// with the site rows
 //   phi_k = sum_{j != k} q_j (k_c / r_kj - tau k_e / f_kj) - tau k_e q_k / R_k
 // and the site-site block A_kl = k_c / r_kl - tau k_e / f_kl (k != l),
 // A_kk = -tau k_e / R_k.  Terms in FP32, sums and the decision in FP64.
-constexpr int MC_MAX_SITE_ATOMS = 128;
+// Stage 1 (k_mc_rows) splits each replica's atoms into MC_CHUNK-atom slices,
+// one block per (slice, replica), and stores per-slice partial rows; stage 2
+// (k_mc_decide) adds the slices in a fixed order, adds the site block, and
+// takes the Metropolis decision -- deterministic, and wide enough to fill the
+// GPU for a handful of replicas.
 
-__device__ __forceinline__ float mc_R(const MCArgs& A, int64_t g) {
-    return A.R ? A.R[g] : A.Rh[g].x;
+struct MCPick {
+    int site, cur, nxt;
+    u64 w2;
+};
+
+// Site and state proposal of replica r (Sec. III.A, III.A.1).
+__device__ __forceinline__ MCPick mc_pick(const MCArgs& A, int r) {
+    const u64 step = (A.ctr ? A.ctr[0] : 0) + A.step;
+    const Philox4 w = philox4x64((u64)r, step, 1 + (u64)A.kind, 0, A.seed, 0);
+    MCPick pk;
+    pk.site = -1;
+    pk.cur = pk.nxt = 0;
+    pk.w2 = w.w[2];
+    int n_kind = 0;
+    for (int s = A.site_off[r]; s < A.site_off[r + 1]; ++s) n_kind += (A.site_kind[s] == A.kind);
+    if (n_kind == 0) return pk;
+    const int want = pick_int(w.w[0], n_kind);
+    for (int s = A.site_off[r], c = 0; s < A.site_off[r + 1]; ++s)
+        if (A.site_kind[s] == A.kind) {
+            if (c == want) { pk.site = s; break; }
+            ++c;
+        }
+    pk.cur = A.state[pk.site];
+    const int k = pick_int(w.w[1], A.site_nstates[pk.site] - 1);
+    pk.nxt = (k < pk.cur) ? k : k + 1;
+    return pk;
 }
 
-__global__ void __launch_bounds__(256) k_mc(MCArgs A) {
-    __shared__ int s_site, s_new, s_cur;
-    __shared__ u64 s_w2;
+// (R, 1/(2R)) of atom g, from whichever radius buffer the caller gave.
+__device__ __forceinline__ float2 mc_Rh(const MCArgs& A, int64_t g) {
+    if (A.R) {
+        const float R = A.R[g];
+        return make_float2(R, 0.5f * __frcp_rn(R));
+    }
+    return A.Rh[g];
+}
+
+__device__ __forceinline__ float mc_pair_term(float4 xk, float2 Rk, float4 xj, float2 Rj, float tke, float kc) {
+    const float dx = xj.x - xk.x, dy = xj.y - xk.y, dz = xj.z - xk.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float e = __expf(-r2 * (Rk.y * Rj.y));          // exp(-r^2 / (4 R_k R_j))
+    const float f2 = fmaf(Rk.x * Rj.x, e, r2);
+    return kc * rsqrtf(r2) - tke * rsqrtf(f2);
+}
+
+__global__ void __launch_bounds__(256) k_mc_rows(MCArgs A) {
+    __shared__ MCPick s_pick;
+    const int r = blockIdx.y, part = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    if (tid == 0) s_pick = mc_pick(A, r);
+    __syncthreads();
+    const int site = s_pick.site;
+    if (site < 0) return;
+    const int a0 = A.site_atom_off[site];
+    const int na = A.site_atom_off[site + 1] - a0;
+    if (na > MC_MAX_SITE_ATOMS || na < 1) return;
+    const int64_t base = A.atom_off[r];
+    const int n = (int)(A.atom_off[r + 1] - base);
+    const int j0 = part * MC_CHUNK, j1 = min(n, j0 + MC_CHUNK);
+    const float tke = (float)A.tau_ke, kc = (float)A.kc;
+    double* out = A.phi_part + ((size_t)r * A.n_parts + part) * MC_MAX_SITE_ATOMS;
+    for (int k = wid; k < na; k += nw) {
+        const int lk = A.site_atom_idx[a0 + k];
+        const int64_t gk = base + lk;
+        const float4 xk = A.xyzq[gk];
+        const float2 Rk = mc_Rh(A, gk);
+        double acc = 0.0;
+        for (int j = j0 + lane; j < j1; j += 32) {
+            const int64_t gj = base + j;
+            const float4 xj = A.xyzq[gj];
+            const float term = (j == lk) ? -tke / Rk.x : mc_pair_term(xk, Rk, xj, mc_Rh(A, gj), tke, kc);
+            acc += (double)(xj.w * term);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) out[k] = acc;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_mc_decide(MCArgs A) {
+    __shared__ MCPick s_pick;
     __shared__ double s_phi[MC_MAX_SITE_ATOMS];
     __shared__ double s_dq[MC_MAX_SITE_ATOMS];
     __shared__ double sh[32];
     __shared__ int s_acc;
     const int r = blockIdx.x;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_pick = mc_pick(A, r);
+    __syncthreads();
+    const int site = s_pick.site;
+    const int a0 = site >= 0 ? A.site_atom_off[site] : 0;
+    const int na = site >= 0 ? A.site_atom_off[site + 1] - a0 : 0;
+    if (site < 0 || na > MC_MAX_SITE_ATOMS || na < 1) {
+        if (tid == 0) {
+            if (A.dG_out) A.dG_out[r] = site < 0 ? 0.0 : __longlong_as_double(0x7ff8000000000000LL);
+            if (A.acc_out) A.acc_out[r] = 0;
+        }
+        return;
+    }
     const int64_t base = A.atom_off[r];
     const int n = (int)(A.atom_off[r + 1] - base);
-    if (tid == 0) {
-        const u64 step = (A.ctr ? A.ctr[0] : 0) + A.step;
-        const Philox4 w = philox4x64((u64)r, step, 1 + (u64)A.kind, 0, A.seed, 0);
-        int n_kind = 0;
-        for (int s = A.site_off[r]; s < A.site_off[r + 1]; ++s) n_kind += (A.site_kind[s] == A.kind);
-        s_site = -1;
-        if (n_kind > 0) {
-            const int want = pick_int(w.w[0], n_kind);
-            for (int s = A.site_off[r], c = 0; s < A.site_off[r + 1]; ++s)
-                if (A.site_kind[s] == A.kind) {
-                    if (c == want) { s_site = s; break; }
-                    ++c;
-                }
-            const int cur = A.state[s_site];
-            const int k = pick_int(w.w[1], A.site_nstates[s_site] - 1);
-            s_cur = cur;
-            s_new = (k < cur) ? k : k + 1;
-            s_w2 = w.w[2];
-        }
-    }
-    __syncthreads();
-    const int site = s_site;
-    if (site < 0) {
-        if (tid == 0) {
-            if (A.dG_out) A.dG_out[r] = 0.0;
-            if (A.acc_out) A.acc_out[r] = 0;
-        }
-        return;
-    }
-    const int a0 = A.site_atom_off[site];
-    const int na = A.site_atom_off[site + 1] - a0;
-    if (na > MC_MAX_SITE_ATOMS || na < 0) {   // rejected on the host; never index past the buffers
-        if (tid == 0) {
-            if (A.dG_out) A.dG_out[r] = __longlong_as_double(0x7ff8000000000000LL);
-            if (A.acc_out) A.acc_out[r] = 0;
-        }
-        return;
-    }
-    const int qo = A.site_q_off[site] + s_new * na;
+    const int n_parts_r = (n + MC_CHUNK - 1) / MC_CHUNK;
+    const int qo = A.site_q_off[site] + s_pick.nxt * na;
     for (int k = tid; k < na; k += blockDim.x) {
         const int64_t gk = base + A.site_atom_idx[a0 + k];
         s_dq[k] = (double)A.q_state[qo + k] - (double)A.xyzq[gk].w;
-    }
-    const float tke = (float)A.tau_ke, kc = (float)A.kc;
-    // site rows: warp w handles site atoms k = w, w + nw, ...
-    for (int k = wid; k < na; k += nw) {
-        const int lk = A.site_atom_idx[a0 + k];
-        const int64_t gk = base + lk;
-        const float4 xk = A.xyzq[gk];
-        const float Rk = mc_R(A, gk);
-        double acc = 0.0;
-        for (int j = lane; j < n; j += 32) {
-            const int64_t gj = base + j;
-            const float4 xj = A.xyzq[gj];
-            float term;
-            if (j == lk) {
-                term = -tke * xj.w / Rk;
-            } else {
-                const float dx = xj.x - xk.x, dy = xj.y - xk.y, dz = xj.z - xk.z;
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                const float Rj = mc_R(A, gj);
-                const float RR = Rk * Rj;
-                const float f2 = fmaf(RR, __expf(-r2 / (4.0f * RR)), r2);
-                term = xj.w * (kc * rsqrtf(r2) - tke * rsqrtf(f2));
-            }
-            acc += (double)term;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) s_phi[k] = acc;
+        double phi = 0.0;
+        for (int p = 0; p < n_parts_r; ++p)
+            phi += A.phi_part[((size_t)r * A.n_parts + p) * MC_MAX_SITE_ATOMS + k];
+        s_phi[k] = phi;
     }
     __syncthreads();
-    // linear term + site-site block, FP64
+    const float tke = (float)A.tau_ke, kc = (float)A.kc;
     double part = 0.0;
     for (int t = tid; t < na * na; t += blockDim.x) {
         const int k = t / na, l = t % na;
         const int64_t gk = base + A.site_atom_idx[a0 + k];
-        double Akl;
+        const float2 Rk = mc_Rh(A, gk);
+        float Akl;
         if (k == l) {
-            Akl = -A.tau_ke / (double)mc_R(A, gk);
+            Akl = -tke / Rk.x;
             part += s_dq[k] * s_phi[k];
         } else {
             const int64_t gl = base + A.site_atom_idx[a0 + l];
-            const float4 xk = A.xyzq[gk], xl = A.xyzq[gl];
-            const double dx = (double)xl.x - xk.x, dy = (double)xl.y - xk.y, dz = (double)xl.z - xk.z;
-            const double r2 = dx * dx + dy * dy + dz * dz;
-            const double RR = (double)mc_R(A, gk) * (double)mc_R(A, gl);
-            const double f = sqrt(r2 + RR * exp(-r2 / (4.0 * RR)));
-            Akl = A.kc / sqrt(r2) - A.tau_ke / f;
+            Akl = mc_pair_term(A.xyzq[gk], Rk, A.xyzq[gl], mc_Rh(A, gl), tke, kc);
         }
-        part += 0.5 * s_dq[k] * s_dq[l] * Akl;
+        part += 0.5 * s_dq[k] * s_dq[l] * (double)Akl;
     }
     const double dE = block_sum_d(part, sh);
     if (tid == 0) {
         const int so = A.site_state_off[site];
-        const int cur = s_cur, nxt = s_new;
+        const int cur = s_pick.cur, nxt = s_pick.nxt;
         double dG = dE - (A.G_ref[so + nxt] - A.G_ref[so + cur]);
         dG += FARADAY * (A.E[r] - A.E0_ref[site]) * (double)(A.n_e[so + nxt] - A.n_e[so + cur]);
         dG += A.kT * LN10 * (A.pH[r] - A.pKa_ref[site]) * (double)(A.n_H[so + nxt] - A.n_H[so + cur]);
-        const double u = unif53(s_w2);
+        const double u = unif53(s_pick.w2);
         const int acc = (dG <= 0.0) || (u < exp(-dG / A.kT));
         if (A.dG_out) A.dG_out[r] = dG;
         if (A.acc_out) A.acc_out[r] = (uint8_t)acc;
@@ -476,7 +514,8 @@ cudaError_t launch_advance_counters(u64* ctr, u64 steps, u64 attempts, cudaStrea
 
 cudaError_t launch_mc(const MCArgs& a, int32_t M, cudaStream_t s) {
     if (M == 0) return cudaSuccess;
-    k_mc<<<M, 256, 0, s>>>(a);
+    if (a.n_parts > 0) k_mc_rows<<<dim3((unsigned)a.n_parts, (unsigned)M), 256, 0, s>>>(a);
+    k_mc_decide<<<M, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -78,6 +78,11 @@ def main():
             for v in c[-2::-1]:
                 expr = f"fmaf({expr}, y, {float(v):.9e}f)"
             fh.write(f"__device__ __forceinline__ float gb_poly_{name}(float y) {{\n    return {expr};\n}}\n")
+            # the same polynomial on two values at once (packed FP32x2 FMA)
+            expr = f"make_float2({float(c[-1]):.9e}f, {float(c[-1]):.9e}f)"
+            for v in c[-2::-1]:
+                expr = f"__ffma2_rn({expr}, y, make_float2({float(v):.9e}f, {float(v):.9e}f))"
+            fh.write(f"__device__ __forceinline__ float2 gb_poly_{name}2(float2 y) {{\n    return {expr};\n}}\n")
     for name, (deg, c, err) in best.items():
         print(name, deg, err)
 

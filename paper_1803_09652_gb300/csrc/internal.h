@@ -29,8 +29,9 @@ struct PairArgs {
     int64_t N;
 };
 
-// One warp task: replica, first (I, J) 32-atom tile pair, number of tile pairs.
-// Tile pairs of a replica are walked row by row over the upper triangle I <= J.
+// One warp task: replica, super-row K (atoms 64K .. 64K+63), first tile J
+// (atoms 32J .. 32J+31, J >= 2K) and number of tiles; the walk continues
+// along the super-row, then into the next super-rows and replicas.
 struct TaskList {
     int4* d_tasks = nullptr;
     int n_tasks = 0;
@@ -43,6 +44,9 @@ enum { EF_ENERGY = 1, EF_PHI = 2, EF_REP = 4 };
 
 cudaError_t launch_pairs(int pass, int flags, const PairArgs& a, const TaskList& t,
                          int warps_per_block, cudaStream_t s);
+
+// Work units (32-atom tiles against 64-atom super-rows) of an n-atom replica.
+int64_t pair_units(int64_t n);
 
 // O(N) kernels --------------------------------------------------------------
 
@@ -90,6 +94,10 @@ cudaError_t launch_md_force_only(const AtomArgs& a, const MDArgs& m, cudaStream_
 cudaError_t launch_set_counters(u64* ctr, u64 step, u64 attempt, cudaStream_t s);
 cudaError_t launch_advance_counters(u64* ctr, u64 steps, u64 attempts, cudaStream_t s);
 
+// Monte Carlo: site rows are summed over MC_CHUNK-atom slices of a replica.
+constexpr int MC_MAX_SITE_ATOMS = 128;
+constexpr int MC_CHUNK = 256;
+
 struct MCArgs {
     const int64_t* atom_off;
     const int32_t* site_off;
@@ -119,6 +127,8 @@ struct MCArgs {
     int32_t* state;
     double* dG_out;
     uint8_t* acc_out;
+    double* phi_part;          // [M][n_parts][MC_MAX_SITE_ATOMS] slice partials (workspace)
+    int32_t n_parts;           // slices of the largest replica
 };
 
 cudaError_t launch_mc(const MCArgs& a, int32_t M, cudaStream_t s);

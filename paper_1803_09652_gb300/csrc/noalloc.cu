@@ -65,8 +65,9 @@ int scratch_for_current_device(unsigned char** out) {
     return GB_OK;
 }
 
-// Work list of one molecule: run w covers tile pairs [w*tpt, (w+1)*tpt) of the
-// row-major upper triangle of nb tiles.  Also writes atom_off = {0, n}.
+// Work list of one molecule: run w covers work units [w*tpt, (w+1)*tpt) of the
+// pair walk (super-rows K of 64 atoms against tiles J = 2K .. nb-1).  Also
+// writes atom_off = {0, n}.
 __global__ void k_static_tasks(int n, int nb, int tpt, int n_tasks, int64_t total, int4* tasks,
                                int64_t* atom_off) {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
@@ -76,13 +77,14 @@ __global__ void k_static_tasks(int n, int nb, int tpt, int n_tasks, int64_t tota
     }
     if (w >= n_tasks) return;
     int64_t p = (int64_t)w * tpt;
-    int I = 0;
-    while (I < nb && p >= nb - I) {
-        p -= nb - I;
-        ++I;
+    const int nk = (nb + 1) / 2;
+    int K = 0;
+    while (K < nk && p >= nb - 2 * K) {
+        p -= nb - 2 * K;
+        ++K;
     }
     const int64_t left = total - (int64_t)w * tpt;
-    tasks[w] = make_int4(0, I, I + (int)p, (int)(left < tpt ? left : tpt));
+    tasks[w] = make_int4(0, K, 2 * K + (int)p, (int)(left < tpt ? left : tpt));
 }
 
 }  // namespace
@@ -102,7 +104,7 @@ extern "C" int gb_energy_forces_static(int32_t n_atoms, const gb_params* params,
     cudaStream_t s = (cudaStream_t)stream;
     const int n = n_atoms;
     const int nb = (n + 31) / 32;
-    const int64_t total = (int64_t)nb * (nb + 1) / 2;
+    const int64_t total = gbk::pair_units(n);
     const int n_tasks = (int)((total + kTilesPerTask - 1) / kTilesPerTask);
 
     gbk::u64* I_acc = (gbk::u64*)(base + kOffI);

@@ -6,8 +6,14 @@
 __device__ __forceinline__ float gb_poly_g(float y) {
     return fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(6.372991085e+00f, y, -3.979435205e+00f), y, 3.000669241e+00f), y, 4.458978176e-01f), y, 9.718360901e-01f), y, 8.843408227e-01f), y, 8.573058248e-01f), y, 7.999977469e-01f), y, 6.666666865e-01f);
 }
+__device__ __forceinline__ float2 gb_poly_g2(float2 y) {
+    return __ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(make_float2(6.372991085e+00f, 6.372991085e+00f), y, make_float2(-3.979435205e+00f, -3.979435205e+00f)), y, make_float2(3.000669241e+00f, 3.000669241e+00f)), y, make_float2(4.458978176e-01f, 4.458978176e-01f)), y, make_float2(9.718360901e-01f, 9.718360901e-01f)), y, make_float2(8.843408227e-01f, 8.843408227e-01f)), y, make_float2(8.573058248e-01f, 8.573058248e-01f)), y, make_float2(7.999977469e-01f, 7.999977469e-01f)), y, make_float2(6.666666865e-01f, 6.666666865e-01f));
+}
 /* h(y), degree 10, max relative error in FP32 Horner 1.47e-07 */
 #define GB_POLY_H_DEG 10
 __device__ __forceinline__ float gb_poly_h(float y) {
     return fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(2.890447998e+02f, y, -3.036016235e+02f), y, 2.056483459e+02f), y, -4.527267456e+01f), y, 2.778405762e+01f), y, 1.125458431e+01f), y, 1.104221439e+01f), y, 8.882757187e+00f), y, 6.857286453e+00f), y, 4.799998760e+00f), y, 2.666666746e+00f);
+}
+__device__ __forceinline__ float2 gb_poly_h2(float2 y) {
+    return __ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(make_float2(2.890447998e+02f, 2.890447998e+02f), y, make_float2(-3.036016235e+02f, -3.036016235e+02f)), y, make_float2(2.056483459e+02f, 2.056483459e+02f)), y, make_float2(-4.527267456e+01f, -4.527267456e+01f)), y, make_float2(2.778405762e+01f, 2.778405762e+01f)), y, make_float2(1.125458431e+01f, 1.125458431e+01f)), y, make_float2(1.104221439e+01f, 1.104221439e+01f)), y, make_float2(8.882757187e+00f, 8.882757187e+00f)), y, make_float2(6.857286453e+00f, 6.857286453e+00f)), y, make_float2(4.799998760e+00f, 4.799998760e+00f)), y, make_float2(2.666666746e+00f, 2.666666746e+00f));
 }

@@ -102,7 +102,10 @@ def test_charge_derivative_sums_to_twice_energy(pkg):
     out, _ = _run(pkg, b)
     q = b.xyzq()[:, 3].astype(np.float64)
     E = out["E"][0, 0] + out["E"][0, 1]
-    assert abs((q * out["dEdq"]).sum() - 2 * E) <= 2e-6 * abs(E)
+    # both sides are sums of the same FP32 pair terms rounded differently:
+    # bound by FP32 resolution on the sum of magnitudes, not on the cancelled total
+    scale = np.abs(q * out["dEdq"]).sum()
+    assert abs((q * out["dEdq"]).sum() - 2 * E) <= 2e-6 * scale
 
 
 def test_net_force_vanishes(pkg):
