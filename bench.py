@@ -242,12 +242,16 @@ def site_reference_energies_gpu(pkg, batch, dev, params):
     return G
 
 
-def launches_per_segment(md_steps):
+def launches_per_segment(md_steps, persistent=True):
     """Kernels of this library enqueued by one gb_md_segment call of md_steps."""
-    per_md = 7                                     # first half, 3 pair passes, 2 finalizers, second half
-    mc = 2 * (md_steps // MC_EVERY)                # protonation + redox attempt kernels
+    n_mc = md_steps // MC_EVERY
+    mc = 4 * n_mc                                  # (slice rows + decision) x (protonation, redox)
     ex = 2 * (md_steps // EX_EVERY)                # exchange + attempt counter
-    return 1 + per_md * md_steps + mc + ex + 1     # + set counters, + advance step counter
+    if persistent:
+        md = n_mc                                  # one persistent launch per run between MC points
+    else:
+        md = 8 * md_steps                          # halves, boxes, 3 pair passes, 2 transforms
+    return 1 + md + mc + ex + 1                    # + set counters, + advance step counter
 
 
 def main():
@@ -258,7 +262,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--persistent", action="store_true",
+                    help="one persistent launch per run of MD steps instead of eight launches per step")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
@@ -285,8 +291,10 @@ def main():
     params = pkg.default_params(rep_k=10.0, rep_sigma=2.5)
     b = workload()
     S = Setup(pkg, b, dev, seed=1234 + rank, params=params)
-    if args.autotune:
+    if not args.no_autotune:
         S.ctx.autotune(S.xyzq, S.rad)
+    persistent = args.persistent
+    S.ctx.set_persistent(persistent)
     S.ctx.set_profiling(True)
     stream = torch.cuda.current_stream()
     pairs_md = b.pairs_per_eval()
@@ -313,7 +321,7 @@ def main():
         S.ctx.md_segment(S.st, S.sites, MD_PER_STEP)
         ev[k][1].record(stream)
         torch.cuda.synchronize()
-        pass_ms.append(S.ctx.pass_times())
+        pass_ms.append(S.ctx.persist_times() if persistent else S.ctx.pass_times())
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
@@ -329,15 +337,23 @@ def main():
     rep_steps = b.n_rep * MD_PER_STEP * args.steps * world / dev_s
     pm = np.mean(np.array(pass_ms), axis=0)
 
-    # ---- roofline of the dominant pass (FP32 ALU bound) --------------------------
-    dom = int(np.argmax(pm))
-    name = PASS_NAMES[dom]
-    achieved = pairs_md * FLOPS_PER_PAIR[name] / (pm[dom] * 1e-3) / 1e12
+    # ---- roofline of the dominant kernel (FP32 ALU bound) ------------------------
     sm_max = (clk.get("sm_max_mhz") or 2070.0)
     peak = SM_COUNT * FP32_LANES * 2 * sm_max * 1e6 / 1e12
     sm_load = clk.get("sm_mhz") or sm_max
     peak_load = SM_COUNT * FP32_LANES * 2 * sm_load * 1e6 / 1e12
     all_flops = pairs_md * sum(FLOPS_PER_PAIR.values())
+    if persistent:
+        # one launch runs pm[2] MD steps: three pair passes per step
+        name = "k_md_persist"
+        achieved = all_flops * pm[2] / (pm[1] * 1e-3) / 1e12
+        timing = {"ms_per_md_step_in_kernel": float(pm[0]), "ms_per_launch": float(pm[1]),
+                  "md_steps_per_launch": float(pm[2])}
+    else:
+        dom = int(np.argmax(pm))
+        name = "k_pairs<%s>" % PASS_NAMES[dom]
+        achieved = pairs_md * FLOPS_PER_PAIR[PASS_NAMES[dom]] / (pm[dom] * 1e-3) / 1e12
+        timing = {"pass_ms": dict(zip(PASS_NAMES, [float(v) for v in pm]))}
     step_fp32 = all_flops * MD_PER_STEP * args.steps / dev_s / 1e12
     traffic = read_traffic(name)
 
@@ -366,18 +382,20 @@ def main():
                        "pairs_per_md_step": pairs_md, "l2": "flushed between steps (256 MB write)",
                        "tiles": list(S.ctx.tiles()), "parallelism": "replicas batched on one GPU"},
             "replica_md_steps_per_s": rep_steps,
-            "pass_ms": dict(zip(PASS_NAMES, [float(v) for v in pm])),
+            "kernel_timing": timing,
             "fp32_flops_per_pair": FLOPS_PER_PAIR,
             "fp32_tflops_whole_step": step_fp32,
             "fp32_peak_frac_whole_step": step_fp32 / peak,
-            "roofline": {"bound": "alu", "kernel": f"k_pairs<{name}>", "achieved": achieved,
+            "roofline": {"bound": "alu", "kernel": name, "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "frac_at_load_clock": achieved / peak_load, "traffic": traffic,
                          "peak_source": f"{SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 x {sm_max:.0f} MHz"},
             "plain": plain,
             "e2e": e2e,
             "cpu_baseline": cpu,
-            "gpu_launches": launches_per_segment(MD_PER_STEP) * args.steps,
+            "gpu_launches": launches_per_segment(MD_PER_STEP, persistent) * args.steps,
+            "md_kernel": "persistent (one launch per run between MC points)" if persistent else
+                         "eight launches per MD step",
             "clocks": clk,
             "wall_s_timed": wall,
         }
@@ -412,6 +430,7 @@ def plain_form(pkg, b, dev, params, n_bench):
         sb = synth.Batch([rep], pH=b.pH[r:r + 1], E=b.E[r:r + 1], E_ladder=b.E[r:r + 1])
         S = Setup(pkg, sb, dev, seed=99 + r, params=params)
         S.st.ex_every = 0
+        S.ctx.set_persistent(False)
         setups.append(S)
     for S in setups:
         S.ctx.md_segment(S.st, S.sites, 10)

@@ -90,6 +90,9 @@ int gb_sync_status(gb_ctx* ctx, void* stream);
  * the given inputs and keeps the fastest; gb_set_tiles forces one. */
 int gb_autotune(gb_ctx* ctx, const float* xyzq, const float* rad_screen, void* stream);
 int gb_set_tiles(gb_ctx* ctx, int32_t warps_per_block, int32_t tiles_per_task);
+/* Register cap of the pair kernels: 1 = the compiler's choice, 3 = at most
+ * ~85 registers per thread so that three 256-thread blocks fit per SM. */
+int gb_set_reg_cap(gb_ctx* ctx, int32_t min_blocks_per_sm);
 int gb_get_tiles(const gb_ctx* ctx, int32_t* warps_per_block, int32_t* tiles_per_task);
 
 /* Effective Born radii of every atom (OBC model, Sec. III.D):
@@ -278,6 +281,19 @@ int gb_energy_forces_static(int32_t n_atoms, const gb_params* params, const floa
  * mean_ms[0] Born integrals, [1] energy / direct forces, [2] chain rule. */
 int gb_set_profiling(gb_ctx* ctx, int32_t enable);
 int gb_pass_times(gb_ctx* ctx, double* mean_ms);
+
+/* MD driver kernel choice.  Enabled (when the device can hold the grid;
+ * off by default): every run of MD steps up to the next Monte Carlo or
+ * exchange point is ONE cooperative launch of a persistent kernel whose blocks stay
+ * resident and pass the phases of each step (BAOAB halves, the three pair
+ * passes, the O(N) transforms) through grid-wide barriers; a barrier that
+ * waits too long records GB_ERR_TIMEOUT (see gb_sync_status) instead of
+ * hanging.  Disabled: eight launches per step (the kernels gb_energy_forces
+ * uses, the BAOAB halves and the tile bounding boxes).  With profiling on, gb_persist_times returns out[0] the mean ms per
+ * MD step inside the persistent launches of the last block, out[1] the mean
+ * ms per launch and out[2] the mean steps per launch. */
+int gb_set_persistent(gb_ctx* ctx, int32_t enable);
+int gb_persist_times(gb_ctx* ctx, double* out);
 
 #ifdef __cplusplus
 }

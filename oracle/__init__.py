@@ -64,6 +64,7 @@ def lib():
         _lib.gbo_hct_pair_dr.argtypes = [d, d, d]
         _lib.gbo_philox4x64.argtypes = [P, P, P]
         _lib.gbo_born_radii.argtypes = [i64, P, P, P, C.POINTER(Params), P, P, P, P]
+        _lib.gbo_born_radii_subset.argtypes = [i64, P, P, P, C.POINTER(Params), P, i64, P]
         _lib.gbo_energy_fixed_radii.argtypes = [i64, P, P, P, C.POINTER(Params), P]
         _lib.gbo_energy_forces.argtypes = [i64, P, P, P, P, C.POINTER(Params), P, P, P, P, P]
         _lib.gbo_restraints.argtypes = [i64, P, C.POINTER(Params), P, P]
@@ -108,6 +109,17 @@ def born_radii(x, rho, screen, p: Optional[Params] = None):
     out = {k: np.zeros(n) for k in ("I", "psi", "R", "dRdpsi")}
     lib().gbo_born_radii(n, _p(x), _p(rho), _p(screen), C.byref(p), _p(out["I"]),
                          _p(out["psi"]), _p(out["R"]), _p(out["dRdpsi"]))
+    return out
+
+
+def born_radii_subset(x, rho, screen, idx, p: Optional[Params] = None) -> np.ndarray:
+    """Born radii of the listed atoms only (O(N) each)."""
+    p = p or default_params()
+    x, rho, screen = _d(x).reshape(-1, 3), _d(rho), _d(screen)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    out = np.zeros(idx.size)
+    lib().gbo_born_radii_subset(rho.size, _p(x), _p(rho), _p(screen), C.byref(p), _p(idx), idx.size,
+                                _p(out))
     return out
 
 

@@ -144,19 +144,26 @@ static double dist(const double* x, int64_t i, int64_t j, double d[3]) {
  *   R_i   = 1 / (1/a_i - tanh(alpha psi - beta psi^2 + gamma psi^3) / rho_i)
  *   dR_i/dpsi_i = R_i^2 (1 - tanh^2) (alpha - 2 beta psi + 3 gamma psi^2) / rho_i
  * Any output pointer may be NULL. */
+static double born_integral(int64_t n, const double* x, const double* rho, const double* screen,
+                            const gbo_params* p, int64_t i) {
+    double a_i = rho[i] - p->offset;
+    double I = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+        if (j == i) continue;
+        double d[3];
+        double r = dist(x, i, j, d);
+        double s_j = screen[j] * (rho[j] - p->offset);
+        I += gbo_hct_pair(r, a_i, s_j);
+    }
+    return I;
+}
+
 void gbo_born_radii(int64_t n, const double* x, const double* rho, const double* screen,
                     const gbo_params* p, double* I_out, double* psi_out, double* R_out,
                     double* dRdpsi_out) {
     for (int64_t i = 0; i < n; ++i) {
         double a_i = rho[i] - p->offset;
-        double I = 0.0;
-        for (int64_t j = 0; j < n; ++j) {
-            if (j == i) continue;
-            double d[3];
-            double r = dist(x, i, j, d);
-            double s_j = screen[j] * (rho[j] - p->offset);
-            I += gbo_hct_pair(r, a_i, s_j);
-        }
+        double I = born_integral(n, x, rho, screen, p, i);
         double psi = a_i * I;
         double phi = p->alpha * psi - p->beta * psi * psi + p->gamma * psi * psi * psi;
         double th = tanh(phi);
@@ -167,6 +174,19 @@ void gbo_born_radii(int64_t n, const double* x, const double* rho, const double*
         if (dRdpsi_out)
             dRdpsi_out[i] = R * R * (1.0 - th * th) *
                             (p->alpha - 2.0 * p->beta * psi + 3.0 * p->gamma * psi * psi) / rho[i];
+    }
+}
+
+/* Born radii of the m atoms listed in idx only (same definition as above),
+ * for spot checks of large molecules: R_out[k] is the radius of atom idx[k]. */
+void gbo_born_radii_subset(int64_t n, const double* x, const double* rho, const double* screen,
+                           const gbo_params* p, const int64_t* idx, int64_t m, double* R_out) {
+    for (int64_t k = 0; k < m; ++k) {
+        int64_t i = idx[k];
+        double a_i = rho[i] - p->offset;
+        double psi = a_i * born_integral(n, x, rho, screen, p, i);
+        double phi = p->alpha * psi - p->beta * psi * psi + p->gamma * psi * psi * psi;
+        R_out[k] = 1.0 / (1.0 / a_i - tanh(phi) / rho[i]);
     }
 }
 

@@ -103,6 +103,7 @@ def load(path: Optional[str] = None):
         "gb_sync_status": [_P, _P],
         "gb_autotune": [_P, _P, _P, _P],
         "gb_set_tiles": [_P, i32, i32],
+        "gb_set_reg_cap": [_P, i32],
         "gb_get_tiles": [_P, C.POINTER(i32), C.POINTER(i32)],
         "gb_born_radii": [_P, _P, _P, _P, _P],
         "gb_energy_forces": [_P, _P, _P, _P, _P, _P, _P, _P, _P],
@@ -113,6 +114,8 @@ def load(path: Optional[str] = None):
         "gb_md_segment": [_P, C.POINTER(MDState), C.POINTER(Sites), C.c_int64, _P],
         "gb_set_profiling": [_P, i32],
         "gb_pass_times": [_P, C.POINTER(C.c_double)],
+        "gb_set_persistent": [_P, i32],
+        "gb_persist_times": [_P, C.POINTER(C.c_double)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -249,6 +252,9 @@ class Context:
     def set_tiles(self, warps_per_block: int, tiles_per_task: int):
         _check(self.lib.gb_set_tiles(self.h, warps_per_block, tiles_per_task), self.h)
 
+    def set_reg_cap(self, min_blocks: int):
+        _check(self.lib.gb_set_reg_cap(self.h, int(min_blocks)), self.h)
+
     def tiles(self):
         w, t = C.c_int32(), C.c_int32()
         _check(self.lib.gb_get_tiles(self.h, C.byref(w), C.byref(t)), self.h)
@@ -280,6 +286,16 @@ class Context:
         """Mean ms of the Born, energy and chain passes over the last MD block."""
         arr = (C.c_double * 3)()
         _check(self.lib.gb_pass_times(self.h, arr), self.h)
+        return [float(v) for v in arr]
+
+    def set_persistent(self, on: bool):
+        _check(self.lib.gb_set_persistent(self.h, 1 if on else 0), self.h)
+
+    def persist_times(self):
+        """(ms per MD step, ms per launch, steps per launch) of the persistent
+        launches of the last MD block (profiling on)."""
+        arr = (C.c_double * 3)()
+        _check(self.lib.gb_persist_times(self.h, arr), self.h)
         return [float(v) for v in arr]
 
     def md_segment(self, st: MDState, sites: Optional[SiteTables], nsteps: int, stream=None):

@@ -30,9 +30,12 @@ struct gb_ctx {
     float* cc = nullptr;
     int* err = nullptr;
     double* mc_part = nullptr;          // MC site-row slice partials
+    float4* boxes = nullptr;            // tile bounding boxes
+    int* tile_off = nullptr;
+    int n_tiles32 = 0;
     int32_t mc_parts = 0;
     gbk::TaskList tasks;
-    int wpb = 8;
+    int wpb = 4;
     int tpt = 0;
     int64_t total_tiles = 0;
     std::string msg;
@@ -43,6 +46,12 @@ struct gb_ctx {
     std::vector<cudaEvent_t> prof_ev;
     int64_t prof_steps = 0;
     bool capturing = false;
+    // persistent MD kernel: grid (0 = unavailable), its task list, barrier words
+    int persist_grid = 0;
+    bool use_persist = false;
+    gbk::TaskList ptasks;
+    unsigned* bar = nullptr;
+    std::vector<int> prof_steps_per_launch;
     // cached MD graph
     cudaGraphExec_t md_exec = nullptr;
     std::vector<uint8_t> md_key;
@@ -91,15 +100,15 @@ cudaError_t zalloc(T** p, size_t n) {
 
 // Cut the work of all replicas (super-rows of 64 atoms against 32-atom tiles
 // J >= 2K, replicas in order) into runs of `tpt` tiles, one warp task each.
-int build_tasks(gb_ctx* c) {
+int build_tasks_into(gb_ctx* c, int tpt, gbk::TaskList& out) {
     std::vector<int4> t;
-    t.reserve((size_t)(c->total_tiles / c->tpt + 1));
+    t.reserve((size_t)(c->total_tiles / tpt + 1));
     int64_t left_total = c->total_tiles;
     int r = 0, K = 0, J = 0;
     auto nb_of = [&](int rr) { return (int)((c->off_h[rr + 1] - c->off_h[rr] + 31) / 32); };
     while (r < c->M && nb_of(r) == 0) ++r;
     while (left_total > 0) {
-        const int cnt = (int)std::min<int64_t>(c->tpt, left_total);
+        const int cnt = (int)std::min<int64_t>(tpt, left_total);
         t.push_back(make_int4(r, K, J, cnt));
         left_total -= cnt;
         int64_t k = cnt;
@@ -121,13 +130,32 @@ int build_tasks(gb_ctx* c) {
             }
         }
     }
-    if (c->tasks.d_tasks) cudaFree(c->tasks.d_tasks);
-    c->tasks.d_tasks = nullptr;
-    c->tasks.n_tasks = (int)t.size();
-    GB_CHECK(c, zalloc(&c->tasks.d_tasks, t.size()));
+    if (out.d_tasks) cudaFree(out.d_tasks);
+    out.d_tasks = nullptr;
+    out.n_tasks = (int)t.size();
+    GB_CHECK(c, zalloc(&out.d_tasks, t.size()));
     if (!t.empty())
-        GB_CHECK(c, cudaMemcpy(c->tasks.d_tasks, t.data(), t.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        GB_CHECK(c, cudaMemcpy(out.d_tasks, t.data(), t.size() * sizeof(int4), cudaMemcpyHostToDevice));
     return GB_OK;
+}
+
+int build_tasks(gb_ctx* c) { return build_tasks_into(c, c->tpt, c->tasks); }
+
+// Resident grid of the persistent MD kernel and its task list: the batch's
+// work cut into one run per resident warp.
+int setup_persist(gb_ctx* c) {
+    int dev = 0, sms = 0, per_sm = 0;
+    GB_CHECK(c, cudaGetDevice(&dev));
+    GB_CHECK(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    GB_CHECK(c, gbk::persist_occupancy(c->p.rep_k != 0.0f ? 1 : 0, &per_sm));
+    if (per_sm < 1 || c->total_tiles == 0) {
+        c->persist_grid = 0;
+        return GB_OK;
+    }
+    c->persist_grid = sms * per_sm;
+    const int64_t warps = (int64_t)c->persist_grid * 4;
+    const int tpt = (int)std::max<int64_t>(1, (c->total_tiles + warps - 1) / warps);
+    return build_tasks_into(c, tpt, c->ptasks);
 }
 
 int default_tpt(const gb_ctx* c) {
@@ -155,6 +183,8 @@ gbk::PairArgs pair_args(const gb_ctx* c, const float* xyzq, const float* rad) {
     a.F_acc = c->F_acc;
     a.E_acc = c->E_acc;
     a.N = c->N;
+    a.boxes = c->boxes;
+    a.tile_off = c->tile_off;
     return a;
 }
 
@@ -192,6 +222,7 @@ int evaluate(gb_ctx* c, const float* xyzq, const float* rad, float* R_out, int f
              double* phi_out, cudaStream_t s, const cudaEvent_t* ev = nullptr) {
     const gbk::PairArgs pa = pair_args(c, xyzq, rad);
     const gbk::AtomArgs aa = atom_args(c, xyzq, rad);
+    GB_CHECK(c, gbk::launch_tile_boxes(pa, c->M, c->n_tiles32, s));
     if (ev) GB_CHECK(c, mark(c, ev[0], s));
     GB_CHECK(c, gbk::launch_pairs(gbk::PASS_BORN, 0, pa, c->tasks, c->wpb, s));
     if (ev) GB_CHECK(c, mark(c, ev[1], s));
@@ -274,7 +305,17 @@ extern "C" int gb_ctx_create(gb_ctx** out, int32_t n_rep, const int64_t* atom_of
     step(zalloc(&c->cfac, N));
     step(zalloc(&c->cc, N));
     step(zalloc(&c->err, 1));
+    step(zalloc(&c->bar, 2));
     c->mc_parts = (c->max_n + gbk::MC_CHUNK - 1) / gbk::MC_CHUNK;
+    {
+        std::vector<int> toff(n_rep + 1, 0);
+        for (int r = 0; r < n_rep; ++r) toff[r + 1] = toff[r] + (int)((atom_off[r + 1] - atom_off[r] + 31) / 32);
+        c->n_tiles32 = toff[n_rep];
+        step(zalloc(&c->tile_off, n_rep + 1));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(c->tile_off, toff.data(), sizeof(int) * (n_rep + 1), cudaMemcpyHostToDevice);
+        step(zalloc(&c->boxes, 2 * (size_t)std::max(c->n_tiles32, 1)));
+    }
     step(zalloc(&c->mc_part, (size_t)n_rep * std::max(c->mc_parts, 1) * gbk::MC_MAX_SITE_ATOMS));
     step(cudaStreamCreateWithFlags(&c->cs, cudaStreamNonBlocking));
     step(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
@@ -286,7 +327,9 @@ extern "C" int gb_ctx_create(gb_ctx** out, int32_t n_rep, const int64_t* atom_of
         return code;
     }
     c->tpt = default_tpt(c);
+    c->tasks.min_blocks = 3;
     int rc = build_tasks(c);
+    if (rc == GB_OK) rc = setup_persist(c);
     if (rc != GB_OK) {
         g_create_error = c->msg;
         gb_ctx_destroy(c);
@@ -302,6 +345,8 @@ extern "C" int gb_ctx_destroy(gb_ctx* c) {
     if (c->md_exec) cudaGraphExecDestroy(c->md_exec);
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     cudaFree(c->tasks.d_tasks);
+    cudaFree(c->ptasks.d_tasks);
+    cudaFree(c->bar);
     cudaFree(c->off_d);
     cudaFree(c->I_acc);
     cudaFree(c->dR_acc);
@@ -314,6 +359,8 @@ extern "C" int gb_ctx_destroy(gb_ctx* c) {
     cudaFree(c->cc);
     cudaFree(c->err);
     cudaFree(c->mc_part);
+    cudaFree(c->boxes);
+    cudaFree(c->tile_off);
     if (c->cs) cudaStreamDestroy(c->cs);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
@@ -352,6 +399,14 @@ extern "C" int gb_set_tiles(gb_ctx* c, int32_t wpb, int32_t tpt) {
     return GB_OK;
 }
 
+extern "C" int gb_set_reg_cap(gb_ctx* c, int32_t min_blocks) {
+    if (!c) return fail(nullptr, GB_ERR_INVALID_ARG, "NULL context");
+    if (min_blocks != 1 && min_blocks != 3) return fail(c, GB_ERR_INVALID_ARG, "min_blocks must be 1 or 3");
+    c->tasks.min_blocks = min_blocks;
+    if (c->md_exec) { cudaGraphExecDestroy(c->md_exec); c->md_exec = nullptr; c->md_key.clear(); }
+    return GB_OK;
+}
+
 extern "C" int gb_get_tiles(const gb_ctx* c, int32_t* wpb, int32_t* tpt) {
     if (!c || !wpb || !tpt) return GB_ERR_INVALID_ARG;
     *wpb = c->wpb;
@@ -375,6 +430,7 @@ extern "C" int gb_born_radii(gb_ctx* c, const float* xyzq, const float* rad, flo
     cudaStream_t s = (cudaStream_t)stream;
     const gbk::PairArgs pa = pair_args(c, xyzq, rad);
     const gbk::AtomArgs aa = atom_args(c, xyzq, rad);
+    GB_CHECK(c, gbk::launch_tile_boxes(pa, c->M, c->n_tiles32, s));
     GB_CHECK(c, gbk::launch_pairs(gbk::PASS_BORN, 0, pa, c->tasks, c->wpb, s));
     GB_CHECK(c, gbk::launch_born_finalize(aa, R_out, s));
     return GB_OK;
@@ -517,19 +573,139 @@ int check_md(gb_ctx* c, const gb_md_state* st) {
     return GB_OK;
 }
 
+// Monte Carlo attempts (protonation, then redox) after block step k (1-based):
+// the Philox step is the device counter ctr[0] + k.
+int enqueue_mc(gb_ctx* c, gb_md_state* st, const gb_sites* sites, int64_t k, cudaStream_t s) {
+    for (int kind = 0; kind < 2; ++kind) {
+        gbk::MCArgs a{};
+        a.atom_off = c->off_d;
+        a.site_off = sites->site_off;
+        a.site_kind = sites->site_kind;
+        a.site_nstates = sites->site_nstates;
+        a.site_atom_off = sites->site_atom_off;
+        a.site_atom_idx = sites->site_atom_idx;
+        a.site_state_off = sites->site_state_off;
+        a.site_q_off = sites->site_q_off;
+        a.q_state = sites->q_state;
+        a.G_ref = sites->G_ref;
+        a.n_H = sites->n_H;
+        a.n_e = sites->n_e;
+        a.pKa_ref = sites->pKa_ref;
+        a.E0_ref = sites->E0_ref;
+        a.xyzq = (float4*)st->xyzq;
+        a.R = nullptr;
+        a.Rh = c->Rh;
+        a.pH = st->pH;
+        a.E = st->E;
+        a.kT = st->kT;
+        a.tau_ke = (1.0 / c->p.eps_in - 1.0 / c->p.eps_out) * gbk::KE;
+        a.kc = gbk::KE / c->p.eps_in;
+        a.seed = st->seed;
+        a.step = (u64)k;
+        a.ctr = c->ctr;
+        a.kind = kind;
+        a.state = st->state;
+        a.dG_out = nullptr;
+        a.acc_out = nullptr;
+        a.phi_part = c->mc_part;
+        a.n_parts = c->mc_parts;
+        GB_CHECK(c, gbk::launch_mc(a, c->M, s));
+    }
+    return GB_OK;
+}
+
+// Neighbour exchange on the (pH x E) grid; the attempt number is ctr[1], which
+// the second kernel advances.
+int enqueue_exchange(gb_ctx* c, gb_md_state* st, const gb_sites* sites, cudaStream_t s) {
+    gbk::GridExArgs x{};
+    x.n_pH = st->n_pH;
+    x.n_E = st->n_E;
+    x.E_ladder = st->E_ladder;
+    x.pH_ladder = st->pH_ladder;
+    x.grid = st->grid;
+    x.site_off = sites->site_off;
+    x.site_kind = sites->site_kind;
+    x.site_state_off = sites->site_state_off;
+    x.n_H = sites->n_H;
+    x.n_e = sites->n_e;
+    x.state = st->state;
+    x.ctr = c->ctr;
+    x.ex_dim = st->ex_dim;
+    x.wrap = st->wrap;
+    x.seed = st->seed;
+    x.kT = st->kT;
+    x.E_rep = st->E;
+    x.pH_rep = st->pH;
+    GB_CHECK(c, gbk::launch_grid_exchange(x, s));
+    GB_CHECK(c, gbk::launch_advance_counters(c->ctr, 0, 1, s));
+    return GB_OK;
+}
+
 // Enqueue `len` MD steps (with their MC attempts and exchanges) on stream s.
 // Steps are numbered from the device counter ctr[0]; the last node advances it.
+// With the persistent kernel every run of steps up to the next MC / exchange
+// point is one launch; otherwise each step is seven launches.
 int enqueue_steps(gb_ctx* c, gb_md_state* st, const gb_sites* sites, int64_t len, cudaStream_t s) {
     const float* xyzq = st->xyzq;
     const float* rad = st->rad_screen;
     const gbk::AtomArgs aa = atom_args(c, xyzq, rad);
     const gbk::MDArgs m = md_args(c, st);
     const int flags = (c->p.rep_k != 0.0f) ? gbk::EF_REP : 0;
-    int64_t n_ex = 0;
+    auto mc_due = [&](int64_t t) { return sites && st->mc_every > 0 && t % st->mc_every == 0; };
+    auto ex_due = [&](int64_t t) { return sites && st->grid && st->ex_every > 0 && t % st->ex_every == 0; };
+    if (c->use_persist && c->persist_grid > 0) {
+        gbk::PersistArgs a{};
+        a.pa = pair_args(c, xyzq, rad);
+        a.aa = aa;
+        a.md = m;
+        a.tasks = c->ptasks.d_tasks;
+        a.n_tasks = c->ptasks.n_tasks;
+        a.M = c->M;
+        a.total_tiles = c->n_tiles32;
+        a.R_out = st->R;
+        a.bar = c->bar;
+        a.err = c->err;
+        if (c->prof) {
+            int rc = ensure_prof_events(c, len);
+            if (rc) return rc;
+            c->prof_steps_per_launch.clear();
+        }
+        int64_t k = 0;
+        while (k < len) {
+            int64_t run = 0;
+            for (int64_t kk = k; kk < len; ++kk) {
+                ++run;
+                const int64_t t = (int64_t)st->step + kk + 1;
+                if (mc_due(t) || ex_due(t)) break;
+            }
+            a.nsteps = (int)run;
+            a.step0 = (int)k;
+            const size_t pe = 2 * c->prof_steps_per_launch.size();
+            if (c->prof) GB_CHECK(c, mark(c, c->prof_ev[pe], s));
+            GB_CHECK(c, gbk::launch_persist(a, flags ? 1 : 0, c->persist_grid, s));
+            if (c->prof) {
+                GB_CHECK(c, mark(c, c->prof_ev[pe + 1], s));
+                c->prof_steps_per_launch.push_back((int)run);
+            }
+            k += run;
+            const int64_t t = (int64_t)st->step + k;
+            if (mc_due(t)) {
+                int rc = enqueue_mc(c, st, sites, k, s);
+                if (rc) return rc;
+            }
+            if (ex_due(t)) {
+                int rc = enqueue_exchange(c, st, sites, s);
+                if (rc) return rc;
+            }
+        }
+        GB_CHECK(c, gbk::launch_advance_counters(c->ctr, (u64)len, 0, s));
+        return GB_OK;
+    }
     if (c->prof) {
         int rc = ensure_prof_events(c, len);
         if (rc) return rc;
         c->prof_steps = len;
+        c->prof_steps_per_launch.clear();
     }
     for (int64_t k = 0; k < len; ++k) {
         GB_CHECK(c, gbk::launch_md_first(aa, m, (int)k, s));
@@ -538,66 +714,13 @@ int enqueue_steps(gb_ctx* c, gb_md_state* st, const gb_sites* sites, int64_t len
         if (rc) return rc;
         GB_CHECK(c, gbk::launch_md_second(aa, m, s));
         const int64_t t = (int64_t)st->step + k + 1;   // only its residues matter
-        if (sites && st->mc_every > 0 && t % st->mc_every == 0) {
-            for (int kind = 0; kind < 2; ++kind) {
-                gbk::MCArgs a{};
-                a.atom_off = c->off_d;
-                a.site_off = sites->site_off;
-                a.site_kind = sites->site_kind;
-                a.site_nstates = sites->site_nstates;
-                a.site_atom_off = sites->site_atom_off;
-                a.site_atom_idx = sites->site_atom_idx;
-                a.site_state_off = sites->site_state_off;
-                a.site_q_off = sites->site_q_off;
-                a.q_state = sites->q_state;
-                a.G_ref = sites->G_ref;
-                a.n_H = sites->n_H;
-                a.n_e = sites->n_e;
-                a.pKa_ref = sites->pKa_ref;
-                a.E0_ref = sites->E0_ref;
-                a.xyzq = (float4*)st->xyzq;
-                a.R = nullptr;
-                a.Rh = c->Rh;
-                a.pH = st->pH;
-                a.E = st->E;
-                a.kT = st->kT;
-                a.tau_ke = (1.0 / c->p.eps_in - 1.0 / c->p.eps_out) * gbk::KE;
-                a.kc = gbk::KE / c->p.eps_in;
-                a.seed = st->seed;
-                a.step = (u64)(k + 1);
-                a.ctr = c->ctr;
-                a.kind = kind;
-                a.state = st->state;
-                a.dG_out = nullptr;
-                a.acc_out = nullptr;
-                a.phi_part = c->mc_part;
-                a.n_parts = c->mc_parts;
-                GB_CHECK(c, gbk::launch_mc(a, c->M, s));
-            }
+        if (mc_due(t)) {
+            rc = enqueue_mc(c, st, sites, k + 1, s);
+            if (rc) return rc;
         }
-        if (sites && st->grid && st->ex_every > 0 && t % st->ex_every == 0) {
-            gbk::GridExArgs x{};
-            x.n_pH = st->n_pH;
-            x.n_E = st->n_E;
-            x.E_ladder = st->E_ladder;
-            x.pH_ladder = st->pH_ladder;
-            x.grid = st->grid;
-            x.site_off = sites->site_off;
-            x.site_kind = sites->site_kind;
-            x.site_state_off = sites->site_state_off;
-            x.n_H = sites->n_H;
-            x.n_e = sites->n_e;
-            x.state = st->state;
-            x.ctr = c->ctr;
-            x.ex_dim = st->ex_dim;
-            x.wrap = st->wrap;
-            x.seed = st->seed;
-            x.kT = st->kT;
-            x.E_rep = st->E;
-            x.pH_rep = st->pH;
-            GB_CHECK(c, gbk::launch_grid_exchange(x, s));
-            GB_CHECK(c, gbk::launch_advance_counters(c->ctr, 0, 1, s));
-            ++n_ex;
+        if (ex_due(t)) {
+            rc = enqueue_exchange(c, st, sites, s);
+            if (rc) return rc;
         }
     }
     GB_CHECK(c, gbk::launch_advance_counters(c->ctr, (u64)len, 0, s));
@@ -658,7 +781,7 @@ extern "C" int gb_md_segment(gb_ctx* c, gb_md_state* st, const gb_sites* sites, 
         gb_sites ks{};
         if (sites) ks = *sites;
         memcpy(key.data() + sizeof(kst), &ks, sizeof(ks));
-        const int64_t extra[3] = {L, c->wpb, (int64_t)c->tpt * 2 + (c->prof ? 1 : 0)};
+        const int64_t extra[3] = {L, c->wpb * 2 + (c->use_persist ? 1 : 0), (int64_t)c->tpt * 2 + (c->prof ? 1 : 0)};
         memcpy(key.data() + sizeof(kst) + sizeof(ks), extra, sizeof(extra));
         if (c->prof) {
             rc = ensure_prof_events(c, L);
@@ -714,12 +837,14 @@ extern "C" int gb_autotune(gb_ctx* c, const float* xyzq, const float* rad, void*
     GB_CHECK(c, cudaEventCreate(&e0));
     GB_CHECK(c, cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_w = c->wpb, best_t = c->tpt;
+    int best_w = c->wpb, best_t = c->tpt, best_m = c->tasks.min_blocks;
     for (int t : tpts) {
         rc = gb_set_tiles(c, c->wpb, t);
         if (rc) break;
-        for (int w : wpbs) {
+        for (int cfg = 0; cfg < 4; ++cfg) {
+            const int w = wpbs[cfg & 1];
             c->wpb = w;
+            c->tasks.min_blocks = (cfg & 2) ? 3 : 1;
             float ms_min = 1e30f;
             for (int rep = 0; rep < 3; ++rep) {
                 cudaEventRecord(e0, s);
@@ -734,13 +859,14 @@ extern "C" int gb_autotune(gb_ctx* c, const float* xyzq, const float* rad, void*
                 if (rep > 0) ms_min = std::min(ms_min, ms);
             }
             if (rc) break;
-            if (ms_min < best) { best = ms_min; best_w = w; best_t = t; }
+            if (ms_min < best) { best = ms_min; best_w = w; best_t = t; best_m = c->tasks.min_blocks; }
         }
         if (rc) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
+    c->tasks.min_blocks = best_m;
     return gb_set_tiles(c, best_w, best_t);
 }
 
@@ -753,7 +879,8 @@ extern "C" int gb_set_profiling(gb_ctx* c, int32_t enable) {
 
 extern "C" int gb_pass_times(gb_ctx* c, double* mean_ms) {
     if (!c || !mean_ms) return fail(c, GB_ERR_INVALID_ARG, "NULL argument");
-    if (!c->prof || c->prof_steps == 0) return fail(c, GB_ERR_INVALID_ARG, "profiling is off or no segment ran");
+    if (!c->prof || c->prof_steps == 0 || !c->prof_steps_per_launch.empty())
+        return fail(c, GB_ERR_INVALID_ARG, "profiling is off or no three-pass segment ran");
     DeviceGuard g(c->device);
     for (int p = 0; p < 3; ++p) {
         double acc = 0.0;
@@ -765,5 +892,32 @@ extern "C" int gb_pass_times(gb_ctx* c, double* mean_ms) {
         }
         mean_ms[p] = acc / (double)c->prof_steps;
     }
+    return GB_OK;
+}
+
+extern "C" int gb_set_persistent(gb_ctx* c, int32_t enable) {
+    if (!c) return fail(nullptr, GB_ERR_INVALID_ARG, "NULL context");
+    c->use_persist = enable != 0;
+    if (c->md_exec) { cudaGraphExecDestroy(c->md_exec); c->md_exec = nullptr; c->md_key.clear(); }
+    return GB_OK;
+}
+
+extern "C" int gb_persist_times(gb_ctx* c, double* out) {
+    if (!c || !out) return fail(c, GB_ERR_INVALID_ARG, "NULL argument");
+    if (!c->prof || c->prof_steps_per_launch.empty())
+        return fail(c, GB_ERR_INVALID_ARG, "profiling is off or no persistent launch ran");
+    DeviceGuard g(c->device);
+    double ms_sum = 0.0, steps = 0.0;
+    for (size_t k = 0; k < c->prof_steps_per_launch.size(); ++k) {
+        float ms = 0.0f;
+        GB_CHECK(c, cudaEventSynchronize(c->prof_ev[2 * k + 1]));
+        GB_CHECK(c, cudaEventElapsedTime(&ms, c->prof_ev[2 * k], c->prof_ev[2 * k + 1]));
+        ms_sum += ms;
+        steps += c->prof_steps_per_launch[k];
+    }
+    const double nl = (double)c->prof_steps_per_launch.size();
+    out[0] = ms_sum / steps;   // ms per MD step inside the persistent kernel
+    out[1] = ms_sum / nl;      // ms per launch
+    out[2] = steps / nl;       // MD steps per launch
     return GB_OK;
 }

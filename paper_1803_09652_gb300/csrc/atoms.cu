@@ -3,8 +3,7 @@
 // changes (Eq. 8, 9), replica exchange (Eq. 14, 15).
 #include <cmath>
 
-#include "common.cuh"
-#include "internal.h"
+#include "atoms_impl.cuh"
 
 namespace gbk {
 
@@ -21,42 +20,14 @@ __device__ __forceinline__ double block_sum_d(double v, double* sh) {
     return t;  // valid in thread 0
 }
 
-__device__ __forceinline__ void set_err(int* err, int code) { atomicCAS(err, 0, code); }
-
-// --- Born radii: I -> psi -> R (OBC) -------------------------------------------
-// R = 1 / (1/a - tanh(Phi)/rho), Phi = alpha psi - beta psi^2 + gamma psi^3.
-// Written without cancellation: with t = exp(-2|Phi|) and d = rho - a (exact
-// in FP32), 1/a - tanh(Phi)/rho = (d (1 + t) + 2 a t) / (a rho (1 + t)) for
-// Phi >= 0, and 1 - tanh^2 = 4 t / (1 + t)^2.  The integral is read in FP64.
+// --- Born radii: I -> psi -> R (OBC), see born_finalize_atom ----------------------
 __global__ void k_born_finalize(AtomArgs A, float* R_out) {
     const int r = blockIdx.y;
     const int64_t base = A.atom_off[r];
     const int n = (int)(A.atom_off[r + 1] - base);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int64_t g = base + i;
-    const float I = (float)((double)(long long)A.I_acc[g] * FIX_I_INV);
-    A.I_acc[g] = 0;
-    const float2 rs = A.rad[g];
-    const float rho = rs.x;
-    const float a = rho - A.offset;
-    const float d = rho - a;
-    const float psi = a * I;
-    const float Phi = psi * fmaf(psi, fmaf(A.gamma, psi, -A.beta), A.alpha);
-    const float t = __expf(-2.0f * fabsf(Phi));
-    const float onet = 1.0f + t;
-    float R;
-    if (Phi >= 0.0f) {
-        R = (a * rho * onet) / fmaf(d, onet, 2.0f * a * t);
-    } else {  // tanh < 0: 1/a + |tanh|/rho, no cancellation either
-        R = 1.0f / (1.0f / a + (1.0f - t) / (onet * rho));
-    }
-    const float sech2 = 4.0f * t / (onet * onet);
-    const float dRdpsi = R * R * sech2 * fmaf(psi, fmaf(3.0f * A.gamma, psi, -2.0f * A.beta), A.alpha) / rho;
-    if (!(R > 0.0f) || !isfinite(R) || !isfinite(dRdpsi)) set_err(A.err, GB_ERR_NONFINITE);
-    A.Rh[g] = make_float2(R, 0.5f / R);
-    A.cfac[g] = dRdpsi * a;
-    if (R_out) R_out[g] = R;
+    born_finalize_atom(A, base + i, R_out);
 }
 
 // --- self terms, dE/dR -> chain factor, dE/dq readout ----------------------------
@@ -69,11 +40,8 @@ __global__ void k_energy_finalize(AtomArgs A, int want_energy, double* phi_out) 
     double eself = 0.0;
     if (i < n) {
         const int64_t g = base + i;
-        const double q = A.xyzq[g].w;
-        const double R = A.Rh[g].x;
-        const double dEdR = unfix(A.dR_acc[g]) + 0.5 * A.tau_ke * q * q / (R * R);
-        A.dR_acc[g] = 0;
-        A.cc[g] = (float)(dEdR * (double)A.cfac[g]);
+        double R;
+        const double q = chain_factor_atom(A, g, &R);
         eself = -0.5 * A.tau_ke * q * q / R;
         if (phi_out) {
             phi_out[g] = unfix(A.phi_acc[g]) - A.tau_ke * q / R;
@@ -116,21 +84,6 @@ __global__ void k_forces_out(AtomArgs A, int64_t* F_fixed, float* F_out, double*
 }
 
 // --- Langevin BAOAB ---------------------------------------------------------------
-// Standard normals from Philox4x64-10 (key (seed, 0), counter (replica, step,
-// 4, atom)) by Box-Muller on (u1, u2) and (u3, u4), u1, u3 in (0, 1].
-__device__ __forceinline__ float3 md_normals(u64 seed, u64 r, u64 step, u64 atom) {
-    const Philox4 w = philox4x64(r, step, 4, atom, seed, 0);
-    const float u1 = (float)(((double)(w.w[0] >> 11) + 1.0) * (1.0 / 9007199254740992.0));
-    const float u2 = (float)unif53(w.w[1]);
-    const float u3 = (float)(((double)(w.w[2] >> 11) + 1.0) * (1.0 / 9007199254740992.0));
-    const float u4 = (float)unif53(w.w[3]);
-    const float m1 = sqrtf(-2.0f * logf(u1)), m2 = sqrtf(-2.0f * logf(u3));
-    float s2, c2, s4, c4;
-    sincospif(2.0f * u2, &s2, &c2);
-    sincospif(2.0f * u4, &s4, &c4);
-    return make_float3(m1 * c2, m1 * s2, m2 * c4);
-}
-
 // B (half kick), A (half drift), O (exact Ornstein-Uhlenbeck), A (half drift)
 __global__ void k_md_first(AtomArgs A, MDArgs m, int step_in_block) {
     const int r = blockIdx.y;
@@ -141,16 +94,7 @@ __global__ void k_md_first(AtomArgs A, MDArgs m, int step_in_block) {
     const int64_t g = base + i;
     const u64 step = m.ctr[0] + (u64)step_in_block + 1;
     float4 x = m.xyzq[g], v = m.vel[g];
-    const float4 f = m.force[g];
-    const float3 z = md_normals(m.seed, (u64)r, step, (u64)i);
-    v.x = fmaf(m.h * m.inv_m, f.x, v.x);
-    v.y = fmaf(m.h * m.inv_m, f.y, v.y);
-    v.z = fmaf(m.h * m.inv_m, f.z, v.z);
-    x.x = fmaf(m.h, v.x, x.x); x.y = fmaf(m.h, v.y, x.y); x.z = fmaf(m.h, v.z, x.z);
-    v.x = fmaf(m.c1, v.x, m.c2 * z.x);
-    v.y = fmaf(m.c1, v.y, m.c2 * z.y);
-    v.z = fmaf(m.c1, v.z, m.c2 * z.z);
-    x.x = fmaf(m.h, v.x, x.x); x.y = fmaf(m.h, v.y, x.y); x.z = fmaf(m.h, v.z, x.z);
+    baoab_first(m, x, v, m.force[g], md_normals(m.seed, (u64)r, step, (u64)i));
     m.xyzq[g] = x;
     m.vel[g] = v;
 }
@@ -170,20 +114,8 @@ __global__ void k_md_second(AtomArgs A, MDArgs m, int kick) {
     A.F_acc[g] = 0;
     A.F_acc[A.N + g] = 0;
     A.F_acc[2 * A.N + g] = 0;
-    const float4 xi = m.xyzq[g];
-    if (m.bond_k != 0.0f) {
-#pragma unroll
-        for (int side = 0; side < 2; ++side) {
-            const int j = side ? i + 1 : i - 1;
-            if (j < 0 || j >= n) continue;
-            const float4 xj = m.xyzq[base + j];
-            const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-            const float rr = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-            // dE/dr = 2 k (r - r0); force on i points along +d when stretched
-            const float s = 2.0f * m.bond_k * (rr - m.bond_r0) / rr;
-            fx = fmaf(s, dx, fx); fy = fmaf(s, dy, fy); fz = fmaf(s, dz, fz);
-        }
-    }
+    const float3 fb = bond_force(m, m.xyzq, base, i, n);
+    fx += fb.x; fy += fb.y; fz += fb.z;
     m.force[g] = make_float4(fx, fy, fz, 0.0f);
     if (kick) {
         float4 v = m.vel[g];

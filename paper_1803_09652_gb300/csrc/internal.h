@@ -27,6 +27,8 @@ struct PairArgs {
     u64* F_acc;                // [3N]  forces x | y | z, 2^32
     u64* E_acc;                // [M*4] E_GB, E_Coul, E_rep, spare, 2^32
     int64_t N;
+    float4* boxes;             // [2 * tiles] bounding boxes of 32-atom tiles (nullable)
+    const int* tile_off;       // [M+1] first tile of each replica
 };
 
 // One warp task: replica, super-row K (atoms 64K .. 64K+63), first tile J
@@ -35,6 +37,7 @@ struct PairArgs {
 struct TaskList {
     int4* d_tasks = nullptr;
     int n_tasks = 0;
+    int min_blocks = 1;        // register cap of the pair kernels: 1 (compiler) or 3 per SM
 };
 
 enum PassKind { PASS_BORN = 0, PASS_ENERGY = 1, PASS_CHAIN = 2 };
@@ -47,6 +50,8 @@ cudaError_t launch_pairs(int pass, int flags, const PairArgs& a, const TaskList&
 
 // Work units (32-atom tiles against 64-atom super-rows) of an n-atom replica.
 int64_t pair_units(int64_t n);
+// Bounding boxes of all tiles (PairArgs::boxes, tile_off); no-op when boxes is null.
+cudaError_t launch_tile_boxes(const PairArgs& a, int M, int total_tiles, cudaStream_t s);
 
 // O(N) kernels --------------------------------------------------------------
 
@@ -174,6 +179,26 @@ struct GridExArgs {
 };
 
 cudaError_t launch_grid_exchange(const GridExArgs& a, cudaStream_t s);
+
+// Persistent MD kernel (persist.cu): nsteps MD steps of the whole batch in one
+// cooperative launch.
+struct PersistArgs {
+    PairArgs pa;
+    AtomArgs aa;
+    MDArgs md;
+    const int4* tasks;         // one task per resident warp (or fewer)
+    int n_tasks;
+    int M;
+    int total_tiles;           // 32-atom tiles of the batch
+    int nsteps;                // MD steps in this launch
+    int step0;                 // index of the first of them in the enqueued block
+    float* R_out;              // Born radii of the last step (nullable)
+    unsigned* bar;             // [2] barrier words, cleared by launch_persist
+    int* err;
+};
+size_t persist_smem();
+cudaError_t persist_occupancy(int rep, int* blocks_per_sm);
+cudaError_t launch_persist(const PersistArgs& a, int rep, int grid, cudaStream_t s);
 
 cudaError_t launch_count(const int32_t* site_off, const int32_t* site_kind,
                          const int32_t* site_state_off, const int32_t* n_H,

@@ -1,564 +1,40 @@
-// O(N^2) pair passes of the GB hot path on sm_103a.
-//
-// Every replica's atoms are cut into 32-atom tiles.  A warp owns a contiguous
-// run of the upper triangle's work, walked as 64-atom super-rows: lane l holds
-// the two atoms 64K + l and 64K + 32 + l ("i", one FP32x2 register pair per
-// quantity) for the whole row, while the 32 atoms of tile J ("j") rotate one
-// lane per step with warp shuffles, carrying their FP32 partial sums.  Each
-// step therefore evaluates two pairs per lane with packed FP32x2 arithmetic
-// (FFMA2 / FMUL2 / FADD2: one issue slot for two lanes' worth of FP32 work)
-// and one set of shuffles, and every unordered pair is evaluated exactly once
-// (Newton's third law).  The first two tiles of a super-row touch the
-// diagonal and are masked.  After each tile the j partials are folded into
-// int64 fixed point with one global atomic per atom and component; the i
-// partials go to int64 registers, flushed when the row ends.  FP32 partials
-// never span more than one 64 x 32 block and integer sums are associative,
-// so results are the same for every run, task split and launch order.
-//
-// Pass 1 (Born integrals), pass 2 (GB + Coulomb energy, direct forces, dE/dR,
-// optional dE/dq and soft repulsion) and pass 3 (Born-radius chain rule)
-// share the walker below; the arithmetic of each pass is in its policy.
-#include "common.cuh"
-#include "internal.h"
-#include "poly_coeffs.h"
+// Launchers of the O(N^2) pair passes; the pass arithmetic and the warp walk
+// are in pairs_impl.cuh (shared with the persistent MD kernel).
+#include "pairs_impl.cuh"
 
 namespace gbk {
 
-// --- HCT descreening integral H(r; a, s), closed form -----------------------------
-// H = (1/4pi) * volume integral of |y - x_i|^-4 over the part of the sphere
-// (centre x_j, radius s) that lies outside the sphere (x_i, a).  Closed form
-// from spherical shells about x_i between L = max(a, |r - s|) and U = r + s;
-// when x_i is engulfed (a < s - r) the full shells between a and s - r add
-// 1/a - 1/L.  It is used only where the spheres overlap (rare): there its
-// terms are O(1) and FP32 keeps them.
-__device__ __noinline__ float hct_closed(float r, float rinv, float a, float s) {
-    if (a >= r + s) return 0.0f;
-    const float U = r + s;
-    const float L = fmaxf(a, fabsf(r - s));
-    const float iU = 1.0f / U, iL = 1.0f / L;
-    const float iU2 = iU * iU, iL2 = iL * iL;
-    float b = (iL - iU) + 0.25f * (r - s * s * rinv) * (iU2 - iL2) + 0.5f * rinv * logf(L * iU);
-    if (a < s - r) b += 2.0f * (1.0f / a - iL);
-    return 0.5f * b;
-}
-
-// -(dH/dr) / r of the closed form.
-__device__ __noinline__ float hct_closed_fr(float r, float rinv, float a, float s) {
-    if (a >= r + s) return 0.0f;
-    const float U = r + s;
-    const float rs = r - s;
-    float L, dL;
-    if (a > fabsf(rs)) { L = a; dL = 0.0f; }
-    else { L = fabsf(rs); dL = rs > 0.0f ? 1.0f : -1.0f; }
-    const float iU = 1.0f / U, iL = 1.0f / L;
-    const float iU2 = iU * iU, iL2 = iL * iL;
-    const float w = r - s * s * rinv;           // r - s^2/r
-    const float dw = 1.0f + s * s * rinv * rinv; // d/dr of w
-    // b = 1/L - 1/U + (w/4)(1/U^2 - 1/L^2) + (1/(2r)) ln(L/U)
-    float db = -dL * iL2 + iU2
-             + 0.25f * dw * (iU2 - iL2)
-             + 0.5f * w * (dL * iL2 * iL - iU2 * iU)
-             - 0.5f * rinv * rinv * logf(L * iU)
-             + 0.5f * rinv * (dL * iL - iU);
-    if (a < s - r) db += 2.0f * dL * iL2;
-    return -0.5f * db * rinv;
-}
-
-// Disjoint spheres (r >= a + s) with x = s/r <= 0.6: H = 1/2 s^3 r^-4 g(x^2) and
-// -(dH/dr)/r = 1/2 s^3 r^-6 h(x^2), with g, h the fitted polynomials: no
-// cancellation and no MUFU.  Every lane evaluates the polynomial; the closed
-// form runs only when some lane of the warp holds an overlapping pair (a warp
-// vote), so the common path carries no divergent branch.
-__device__ __forceinline__ bool far_ok(float r, float lim, float y) { return (r >= lim) && (y <= GB_POLY_YMAX); }
-
-// --- packed FP32x2 helpers ----------------------------------------------------------
-typedef float2 f2;
-__device__ __forceinline__ f2 F2(float v) { return make_float2(v, v); }
-__device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
-
-// MUFU reciprocal square root and base-2 exponential; inputs here are never
-// denormal, so the flush-to-zero forms need no fix-up instructions.
-__device__ __forceinline__ float rsqrt_ftz(float x) {
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float ex2_ftz(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ f2 rsqrt2(f2 x) { return make_float2(rsqrt_ftz(x.x), rsqrt_ftz(x.y)); }
-__device__ __forceinline__ f2 ex22(f2 x) { return make_float2(ex2_ftz(x.x), ex2_ftz(x.y)); }
-
-constexpr float SQRT_LOG2E = 1.2011224087864498f;  // sqrt(log2(e))
-constexpr float LN2 = 0.69314718055994531f;
-constexpr float FAR_R2 = 1.0e30f;                  // r^2 given to masked-off lanes
-
-__device__ __forceinline__ long long warp_sum_ll(long long v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// --- diagonal masks -------------------------------------------------------------------
-// Step k pairs lane l's i atoms with tile atom (l + k) mod 32.  A tile that
-// holds the same atoms as an i half ("diagonal") keeps steps 1..15 and the
-// lower half of step 16, which visit each unordered pair once.  Mode DX: the
-// tile is the x half's own tile and the y half is below the diagonal (off);
-// mode DY: the tile is the y half's own tile (x half fully on).
-enum { M_FULL = 0, M_DX = 1, M_DY = 2 };
-struct Mask {
-    bool x, y;
-};
-template <int MODE>
-__device__ __forceinline__ Mask step_mask(int k, int lane) {
-    const bool diag = (k >= 1 && k <= 15) || (k == 16 && lane < 16);
-    Mask m;
-    m.x = (MODE == M_DX) ? diag : true;
-    m.y = (MODE == M_FULL) ? true : (MODE == M_DY ? diag : false);
-    return m;
-}
-template <int MODE>
-__device__ __forceinline__ f2 keep(f2 v, Mask m) {
-    if (MODE == M_FULL) return v;
-    return make_float2(m.x ? v.x : 0.0f, m.y ? v.y : 0.0f);
-}
-template <int MODE>
-__device__ __forceinline__ f2 safe_r2(f2 r2, Mask m) {
-    if (MODE == M_FULL) return r2;
-    return make_float2(m.x ? r2.x : FAR_R2, m.y ? r2.y : FAR_R2);
-}
-
-// Lanes past a replica's end hold ghost atoms (see ghost_x): zero charge,
-// zero descreening radius, zero chain factor, parked far away.
-__device__ __forceinline__ void load_xas(const PairArgs& A, int64_t base, int n, int i, float& x,
-                                         float& y, float& z, float& a, float& s) {
-    if (i < n) {
-        const float4 p = A.xyzq[base + i];
-        const float2 rs = A.rad[base + i];
-        x = p.x; y = p.y; z = p.z;
-        a = rs.x - A.offset;
-        s = rs.y * a;
-    } else {
-        x = ghost_x(i - n); y = 0.0f; z = 0.0f; a = 1.0f; s = 0.0f;
-    }
-}
-
-// --- pass 1: Born integrals I_i = sum_j H(r_ij; a_i, s_j) -----------------------
-struct Born {
-    struct IState {
-        f2 nx, ny, nz, a, s, s2, hs3;   // nx = -x
-        long long acc0, acc1;
-    };
-    struct JState { float x, y, z, a, s, acc; };
-    struct Part {
-        f2 I;
-        __device__ __forceinline__ void zero() { I = F2(0.0f); }
-    };
-    static __device__ __forceinline__ void load_i(const PairArgs& A, int64_t base, int n, int i0, int lane, IState& st) {
-        float x0, y0, z0, a0, s0, x1, y1, z1, a1, s1;
-        load_xas(A, base, n, i0 + lane, x0, y0, z0, a0, s0);
-        load_xas(A, base, n, i0 + 32 + lane, x1, y1, z1, a1, s1);
-        st.nx = make_float2(-x0, -x1); st.ny = make_float2(-y0, -y1); st.nz = make_float2(-z0, -z1);
-        st.a = make_float2(a0, a1); st.s = make_float2(s0, s1);
-        st.s2 = mul2(st.s, st.s);
-        st.hs3 = mul2(mul2(F2(0.5f), st.s2), st.s);
-        st.acc0 = st.acc1 = 0;
-    }
-    static __device__ __forceinline__ void load_j(const PairArgs& A, int64_t base, int n, int j, JState& st) {
-        load_xas(A, base, n, j, st.x, st.y, st.z, st.a, st.s);
-        st.acc = 0.0f;
-    }
-    template <int FLAGS, int MODE>
-    static __device__ __forceinline__ void pair(const PairArgs&, const IState& i, JState& j, Part& p, Mask m,
-                                                int, int, int) {
-        const f2 dx = add2(F2(j.x), i.nx), dy = add2(F2(j.y), i.ny), dz = add2(F2(j.z), i.nz);
-        const f2 r2 = safe_r2<MODE>(fma2(dx, dx, fma2(dy, dy, mul2(dz, dz))), m);
-        const f2 rinv = rsqrt2(r2);
-        const f2 rinv2 = mul2(rinv, rinv), rinv4 = mul2(rinv2, rinv2);
-        const float sj2 = j.s * j.s;
-        const f2 y_ij = mul2(F2(sj2), rinv2), y_ji = mul2(i.s2, rinv2);
-        f2 h_ij = mul2(F2(0.5f * sj2 * j.s), mul2(rinv4, gb_poly_g2(y_ij)));
-        f2 h_ji = mul2(i.hs3, mul2(rinv4, gb_poly_g2(y_ji)));
-        const f2 r = mul2(r2, rinv);
-        const f2 lim_ij = add2(i.a, F2(j.s)), lim_ji = add2(F2(j.a), i.s);
-        const bool b0 = !far_ok(r.x, lim_ij.x, y_ij.x), b1 = !far_ok(r.y, lim_ij.y, y_ij.y);
-        const bool c0 = !far_ok(r.x, lim_ji.x, y_ji.x), c1 = !far_ok(r.y, lim_ji.y, y_ji.y);
-        if (__any_sync(0xffffffffu, b0 || b1 || c0 || c1)) {
-            if (b0) h_ij.x = hct_closed(r.x, rinv.x, i.a.x, j.s);
-            if (b1) h_ij.y = hct_closed(r.y, rinv.y, i.a.y, j.s);
-            if (c0) h_ji.x = hct_closed(r.x, rinv.x, j.a, i.s.x);
-            if (c1) h_ji.y = hct_closed(r.y, rinv.y, j.a, i.s.y);
-        }
-        h_ij = keep<MODE>(h_ij, m);
-        h_ji = keep<MODE>(h_ji, m);
-        p.I = add2(p.I, h_ij);
-        j.acc += h_ji.x + h_ji.y;
-    }
-    static __device__ __forceinline__ void rotate(JState& j, int src) {
-        j.x = shfl(j.x, src); j.y = shfl(j.y, src); j.z = shfl(j.z, src);
-        j.a = shfl(j.a, src); j.s = shfl(j.s, src); j.acc = shfl(j.acc, src);
-    }
-    static __device__ __forceinline__ void fold_i(IState& i, const Part& p) {
-        i.acc0 += fix_i(p.I.x);
-        i.acc1 += fix_i(p.I.y);
-    }
-    static __device__ __forceinline__ void flush_j(const PairArgs& A, int64_t base, int n, int j, const JState& st) {
-        if (j < n) red_add(&A.I_acc[base + j], fix_i(st.acc));
-    }
-    static __device__ __forceinline__ void flush_i(const PairArgs& A, int, int64_t base, int n, int i0, int lane,
-                                                   const IState& st) {
-        if (i0 + lane < n) red_add(&A.I_acc[base + i0 + lane], st.acc0);
-        if (i0 + 32 + lane < n) red_add(&A.I_acc[base + i0 + 32 + lane], st.acc1);
-    }
-};
-
-// --- pass 2: GB + Coulomb pair energy, direct forces, dE/dR, dE/dq --------------
-// Pair (i, j), both orderings of the double sum together:
-//   e_GB = -tau k_e q_i q_j / f,  f^2 = r^2 + R_i R_j exp(-D),  D = r^2 / (4 R_i R_j)
-//   e_C  =  k_c q_i q_j / r
-//   -(de/dr)/r = k_c q_i q_j / r^3 - tau k_e q_i q_j (1 - exp(-D)/4) / f^3
-//   de/dR_i = tau k_e q_i q_j exp(-D)(1 + D) R_j / (2 f^3)   (and i <-> j)
-//   de/dq_i = (-tau k_e / f + k_c / r) q_j                  (and i <-> j)
-// Each atom carries h = sqrt(log2 e) / (2R) (negated for i), so that
-// exp(-D) = 2^(r^2 (-h_i) h_j) is two multiplies and one ex2.
-struct Energy {
-    struct IState {
-        f2 nx, ny, nz, q, R, nh;
-        long long fx0, fy0, fz0, dR0, phi0, fx1, fy1, fz1, dR1, phi1, egb, ec, er;
-    };
-    struct JState { float x, y, z, q, R, h, fx, fy, fz, dR, phi; };
-    struct Part {
-        f2 sx, sy, sz, dR, phi, egb, ec, er;   // s* = sum of fr d (the i force is -s)
-        __device__ __forceinline__ void zero() {
-            sx = sy = sz = dR = phi = egb = ec = er = F2(0.0f);
-        }
-    };
-    static __device__ __forceinline__ void load_one(const PairArgs& A, int64_t base, int n, int i, float& x,
-                                                    float& y, float& z, float& q, float& R, float& h) {
-        if (i < n) {
-            const float4 p = A.xyzq[base + i];
-            const float2 rh = A.Rh[base + i];
-            x = p.x; y = p.y; z = p.z; q = p.w; R = rh.x; h = rh.y * SQRT_LOG2E;
-        } else {
-            x = ghost_x(i - n); y = 0.0f; z = 0.0f; q = 0.0f; R = 1.0f; h = 0.5f * SQRT_LOG2E;
-        }
-    }
-    static __device__ __forceinline__ void load_i(const PairArgs& A, int64_t base, int n, int i0, int lane, IState& st) {
-        float x0, y0, z0, q0, R0, h0, x1, y1, z1, q1, R1, h1;
-        load_one(A, base, n, i0 + lane, x0, y0, z0, q0, R0, h0);
-        load_one(A, base, n, i0 + 32 + lane, x1, y1, z1, q1, R1, h1);
-        st.nx = make_float2(-x0, -x1); st.ny = make_float2(-y0, -y1); st.nz = make_float2(-z0, -z1);
-        st.q = make_float2(q0, q1); st.R = make_float2(R0, R1); st.nh = make_float2(-h0, -h1);
-        st.fx0 = st.fy0 = st.fz0 = st.dR0 = st.phi0 = 0;
-        st.fx1 = st.fy1 = st.fz1 = st.dR1 = st.phi1 = 0;
-        st.egb = st.ec = st.er = 0;
-    }
-    static __device__ __forceinline__ void load_j(const PairArgs& A, int64_t base, int n, int j, JState& st) {
-        load_one(A, base, n, j, st.x, st.y, st.z, st.q, st.R, st.h);
-        st.fx = st.fy = st.fz = st.dR = st.phi = 0.0f;
-    }
-    template <int FLAGS, int MODE>
-    static __device__ __forceinline__ void pair(const PairArgs& A, const IState& i, JState& j, Part& p, Mask m,
-                                                int i0, int jbase, int k) {
-        const f2 dx = add2(F2(j.x), i.nx), dy = add2(F2(j.y), i.ny), dz = add2(F2(j.z), i.nz);
-        const f2 r2 = safe_r2<MODE>(fma2(dx, dx, fma2(dy, dy, mul2(dz, dz))), m);
-        const f2 rinv = rsqrt2(r2);
-        const f2 rinv2 = mul2(rinv, rinv);
-        const f2 qq = mul2(i.q, F2(j.q));
-        const f2 nDl = mul2(r2, mul2(i.nh, F2(j.h)));                 // -D log2(e)
-        const f2 e = ex22(nDl);                                       // exp(-D)
-        const f2 finv = rsqrt2(fma2(mul2(i.R, F2(j.R)), e, r2));
-        const f2 finv3 = mul2(mul2(finv, finv), finv);
-        const f2 w = mul2(mul2(qq, F2(0.5f * A.tau_ke)), finv3);      // tau k_e q q / (2 f^3)
-        const f2 nu = fma2(F2(0.5f), e, F2(-2.0f));                   // -2 (1 - e/4)
-        const f2 qc = mul2(qq, F2(A.kc));
-        f2 fr = fma2(qc, mul2(rinv2, rinv), mul2(w, nu));
-        f2 G = mul2(mul2(w, e), fma2(nDl, F2(-LN2), F2(1.0f)));        // w e (1 + D)
-        f2 er = F2(0.0f);
-        if (FLAGS & EF_REP) {
-            const float sig2 = A.rep_sigma * A.rep_sigma;
-            const bool n0 = r2.x < sig2, n1 = r2.y < sig2;
-            if (__any_sync(0xffffffffu, n0 || n1)) {
-                const int jj = jbase + ((threadIdx.x + k) & 31);
-                const int ia = i0 + (threadIdx.x & 31), ib = ia + 32;
-                if (n0 && (ia - jj > 1 || jj - ia > 1)) {
-                    const float dd = A.rep_sigma - r2.x * rinv.x;
-                    fr.x = fmaf(2.0f * A.rep_k * dd, rinv.x, fr.x);
-                    er.x = A.rep_k * dd * dd;
-                }
-                if (n1 && (ib - jj > 1 || jj - ib > 1)) {
-                    const float dd = A.rep_sigma - r2.y * rinv.y;
-                    fr.y = fmaf(2.0f * A.rep_k * dd, rinv.y, fr.y);
-                    er.y = A.rep_k * dd * dd;
-                }
-            }
-        }
-        fr = keep<MODE>(fr, m);
-        G = keep<MODE>(G, m);
-        p.sx = fma2(fr, dx, p.sx); p.sy = fma2(fr, dy, p.sy); p.sz = fma2(fr, dz, p.sz);
-        j.fx = fmaf(fr.y, dx.y, fmaf(fr.x, dx.x, j.fx));
-        j.fy = fmaf(fr.y, dy.y, fmaf(fr.x, dy.x, j.fy));
-        j.fz = fmaf(fr.y, dz.y, fmaf(fr.x, dz.x, j.fz));
-        p.dR = fma2(G, F2(j.R), p.dR);
-        j.dR = fmaf(G.y, i.R.y, fmaf(G.x, i.R.x, j.dR));
-        if (FLAGS & EF_PHI) {
-            const f2 P = keep<MODE>(fma2(F2(-A.tau_ke), finv, mul2(F2(A.kc), rinv)), m);
-            p.phi = fma2(P, F2(j.q), p.phi);
-            j.phi = fmaf(P.y, i.q.y, fmaf(P.x, i.q.x, j.phi));
-        }
-        if (FLAGS & EF_ENERGY) {
-            p.egb = add2(p.egb, keep<MODE>(mul2(F2(-A.tau_ke), mul2(qq, finv)), m));
-            p.ec = add2(p.ec, keep<MODE>(mul2(qc, rinv), m));
-            if (FLAGS & EF_REP) p.er = add2(p.er, keep<MODE>(er, m));
-        }
-    }
-    template <int FLAGS>
-    static __device__ __forceinline__ void rotate_f(JState& j, int src) {
-        j.x = shfl(j.x, src); j.y = shfl(j.y, src); j.z = shfl(j.z, src);
-        j.q = shfl(j.q, src); j.R = shfl(j.R, src); j.h = shfl(j.h, src);
-        j.fx = shfl(j.fx, src); j.fy = shfl(j.fy, src); j.fz = shfl(j.fz, src);
-        j.dR = shfl(j.dR, src);
-        if (FLAGS & EF_PHI) j.phi = shfl(j.phi, src);
-    }
-    template <int FLAGS>
-    static __device__ __forceinline__ void fold_i_f(IState& i, const Part& p) {
-        i.fx0 -= fix(p.sx.x); i.fy0 -= fix(p.sy.x); i.fz0 -= fix(p.sz.x); i.dR0 += fix(p.dR.x);
-        i.fx1 -= fix(p.sx.y); i.fy1 -= fix(p.sy.y); i.fz1 -= fix(p.sz.y); i.dR1 += fix(p.dR.y);
-        if (FLAGS & EF_PHI) {
-            i.phi0 += fix(p.phi.x);
-            i.phi1 += fix(p.phi.y);
-        }
-        if (FLAGS & EF_ENERGY) {
-            i.egb += fix(p.egb.x) + fix(p.egb.y);
-            i.ec += fix(p.ec.x) + fix(p.ec.y);
-            if (FLAGS & EF_REP) i.er += fix(p.er.x) + fix(p.er.y);
-        }
-    }
-    template <int FLAGS>
-    static __device__ __forceinline__ void flush_j_f(const PairArgs& A, int64_t base, int n, int j, const JState& st) {
-        if (j < n) {
-            const int64_t g = base + j;
-            red_add(&A.F_acc[g], fix(st.fx));
-            red_add(&A.F_acc[A.N + g], fix(st.fy));
-            red_add(&A.F_acc[2 * A.N + g], fix(st.fz));
-            red_add(&A.dR_acc[g], fix(st.dR));
-            if (FLAGS & EF_PHI) red_add(&A.phi_acc[g], fix(st.phi));
-        }
-    }
-    template <int FLAGS>
-    static __device__ __forceinline__ void flush_i_f(const PairArgs& A, int r, int64_t base, int n, int i0, int lane,
-                                                     const IState& st) {
-        if (i0 + lane < n) {
-            const int64_t g = base + i0 + lane;
-            red_add(&A.F_acc[g], st.fx0);
-            red_add(&A.F_acc[A.N + g], st.fy0);
-            red_add(&A.F_acc[2 * A.N + g], st.fz0);
-            red_add(&A.dR_acc[g], st.dR0);
-            if (FLAGS & EF_PHI) red_add(&A.phi_acc[g], st.phi0);
-        }
-        if (i0 + 32 + lane < n) {
-            const int64_t g = base + i0 + 32 + lane;
-            red_add(&A.F_acc[g], st.fx1);
-            red_add(&A.F_acc[A.N + g], st.fy1);
-            red_add(&A.F_acc[2 * A.N + g], st.fz1);
-            red_add(&A.dR_acc[g], st.dR1);
-            if (FLAGS & EF_PHI) red_add(&A.phi_acc[g], st.phi1);
-        }
-        if (FLAGS & EF_ENERGY) {
-            const long long egb = warp_sum_ll(st.egb), ec = warp_sum_ll(st.ec);
-            const long long er = (FLAGS & EF_REP) ? warp_sum_ll(st.er) : 0;
-            if (lane == 0) {
-                red_add(&A.E_acc[4 * r + 0], egb);
-                red_add(&A.E_acc[4 * r + 1], ec);
-                if (FLAGS & EF_REP) red_add(&A.E_acc[4 * r + 2], er);
-            }
-        }
-    }
-};
-
-// --- pass 3: Born-radius chain rule -------------------------------------------
-// E depends on R_i(psi_i), psi_i = a_i sum_j H(r_ij; a_i, s_j).  With
-// c_i = dE/dR_i * dR_i/dpsi_i * a_i the pair (i, j) carries
-//   -(dE/dr)/r = c_i * (-(dH(r; a_i, s_j)/dr)/r) + c_j * (-(dH(r; a_j, s_i)/dr)/r).
-struct Chain {
-    struct IState {
-        f2 nx, ny, nz, a, s, s2, hs3, c;
-        long long fx0, fy0, fz0, fx1, fy1, fz1;
-    };
-    struct JState { float x, y, z, a, s, c, fx, fy, fz; };
-    struct Part {
-        f2 sx, sy, sz;
-        __device__ __forceinline__ void zero() { sx = sy = sz = F2(0.0f); }
-    };
-    static __device__ __forceinline__ void load_one(const PairArgs& A, int64_t base, int n, int i, float& x,
-                                                    float& y, float& z, float& a, float& s, float& c) {
-        load_xas(A, base, n, i, x, y, z, a, s);
-        c = (i < n) ? A.cc[base + i] : 0.0f;
-    }
-    static __device__ __forceinline__ void load_i(const PairArgs& A, int64_t base, int n, int i0, int lane, IState& st) {
-        float x0, y0, z0, a0, s0, c0, x1, y1, z1, a1, s1, c1;
-        load_one(A, base, n, i0 + lane, x0, y0, z0, a0, s0, c0);
-        load_one(A, base, n, i0 + 32 + lane, x1, y1, z1, a1, s1, c1);
-        st.nx = make_float2(-x0, -x1); st.ny = make_float2(-y0, -y1); st.nz = make_float2(-z0, -z1);
-        st.a = make_float2(a0, a1); st.s = make_float2(s0, s1); st.c = make_float2(c0, c1);
-        st.s2 = mul2(st.s, st.s);
-        st.hs3 = mul2(mul2(F2(0.5f), st.s2), st.s);
-        st.fx0 = st.fy0 = st.fz0 = st.fx1 = st.fy1 = st.fz1 = 0;
-    }
-    static __device__ __forceinline__ void load_j(const PairArgs& A, int64_t base, int n, int j, JState& st) {
-        load_one(A, base, n, j, st.x, st.y, st.z, st.a, st.s, st.c);
-        st.fx = st.fy = st.fz = 0.0f;
-    }
-    template <int FLAGS, int MODE>
-    static __device__ __forceinline__ void pair(const PairArgs&, const IState& i, JState& j, Part& p, Mask m,
-                                                int, int, int) {
-        const f2 dx = add2(F2(j.x), i.nx), dy = add2(F2(j.y), i.ny), dz = add2(F2(j.z), i.nz);
-        const f2 r2 = safe_r2<MODE>(fma2(dx, dx, fma2(dy, dy, mul2(dz, dz))), m);
-        const f2 rinv = rsqrt2(r2);
-        const f2 rinv2 = mul2(rinv, rinv);
-        const float sj2 = j.s * j.s;
-        const f2 y_ij = mul2(F2(sj2), rinv2), y_ji = mul2(i.s2, rinv2);
-        // c_i s_j^3/2 h(y_ij) + c_j s_i^3/2 h(y_ji), times r^-6
-        const f2 t_ij = mul2(mul2(i.c, F2(0.5f * sj2 * j.s)), gb_poly_h2(y_ij));
-        const f2 t_ji = mul2(mul2(F2(j.c), i.hs3), gb_poly_h2(y_ji));
-        const f2 rinv6 = mul2(rinv2, mul2(rinv2, rinv2));
-        f2 fr = mul2(add2(t_ij, t_ji), rinv6);
-        const f2 r = mul2(r2, rinv);
-        const f2 lim_ij = add2(i.a, F2(j.s)), lim_ji = add2(F2(j.a), i.s);
-        const bool b0 = !far_ok(r.x, lim_ij.x, y_ij.x), b1 = !far_ok(r.y, lim_ij.y, y_ij.y);
-        const bool c0 = !far_ok(r.x, lim_ji.x, y_ji.x), c1 = !far_ok(r.y, lim_ji.y, y_ji.y);
-        if (__any_sync(0xffffffffu, b0 || b1 || c0 || c1)) {
-            if (b0 || c0)
-                fr.x = (b0 ? i.c.x * hct_closed_fr(r.x, rinv.x, i.a.x, j.s) : t_ij.x * rinv6.x) +
-                       (c0 ? j.c * hct_closed_fr(r.x, rinv.x, j.a, i.s.x) : t_ji.x * rinv6.x);
-            if (b1 || c1)
-                fr.y = (b1 ? i.c.y * hct_closed_fr(r.y, rinv.y, i.a.y, j.s) : t_ij.y * rinv6.y) +
-                       (c1 ? j.c * hct_closed_fr(r.y, rinv.y, j.a, i.s.y) : t_ji.y * rinv6.y);
-        }
-        fr = keep<MODE>(fr, m);
-        p.sx = fma2(fr, dx, p.sx); p.sy = fma2(fr, dy, p.sy); p.sz = fma2(fr, dz, p.sz);
-        j.fx = fmaf(fr.y, dx.y, fmaf(fr.x, dx.x, j.fx));
-        j.fy = fmaf(fr.y, dy.y, fmaf(fr.x, dy.x, j.fy));
-        j.fz = fmaf(fr.y, dz.y, fmaf(fr.x, dz.x, j.fz));
-    }
-    static __device__ __forceinline__ void rotate(JState& j, int src) {
-        j.x = shfl(j.x, src); j.y = shfl(j.y, src); j.z = shfl(j.z, src);
-        j.a = shfl(j.a, src); j.s = shfl(j.s, src); j.c = shfl(j.c, src);
-        j.fx = shfl(j.fx, src); j.fy = shfl(j.fy, src); j.fz = shfl(j.fz, src);
-    }
-    static __device__ __forceinline__ void fold_i(IState& i, const Part& p) {
-        i.fx0 -= fix(p.sx.x); i.fy0 -= fix(p.sy.x); i.fz0 -= fix(p.sz.x);
-        i.fx1 -= fix(p.sx.y); i.fy1 -= fix(p.sy.y); i.fz1 -= fix(p.sz.y);
-    }
-    static __device__ __forceinline__ void flush_j(const PairArgs& A, int64_t base, int n, int j, const JState& st) {
-        if (j < n) {
-            const int64_t g = base + j;
-            red_add(&A.F_acc[g], fix(st.fx));
-            red_add(&A.F_acc[A.N + g], fix(st.fy));
-            red_add(&A.F_acc[2 * A.N + g], fix(st.fz));
-        }
-    }
-    static __device__ __forceinline__ void flush_i(const PairArgs& A, int, int64_t base, int n, int i0, int lane,
-                                                   const IState& st) {
-        if (i0 + lane < n) {
-            const int64_t g = base + i0 + lane;
-            red_add(&A.F_acc[g], st.fx0);
-            red_add(&A.F_acc[A.N + g], st.fy0);
-            red_add(&A.F_acc[2 * A.N + g], st.fz0);
-        }
-        if (i0 + 32 + lane < n) {
-            const int64_t g = base + i0 + 32 + lane;
-            red_add(&A.F_acc[g], st.fx1);
-            red_add(&A.F_acc[A.N + g], st.fy1);
-            red_add(&A.F_acc[2 * A.N + g], st.fz1);
-        }
-    }
-};
-
-// Energy's helpers carry the flag set; adapt them to the walker's interface.
-template <int FLAGS>
-struct EnergyF : Energy {
-    static __device__ __forceinline__ void rotate(JState& j, int src) { rotate_f<FLAGS>(j, src); }
-    static __device__ __forceinline__ void fold_i(IState& i, const Part& p) { fold_i_f<FLAGS>(i, p); }
-    static __device__ __forceinline__ void flush_j(const PairArgs& A, int64_t b, int n, int j, const JState& s) {
-        flush_j_f<FLAGS>(A, b, n, j, s);
-    }
-    static __device__ __forceinline__ void flush_i(const PairArgs& A, int r, int64_t b, int n, int i0, int lane,
-                                                   const IState& s) {
-        flush_i_f<FLAGS>(A, r, b, n, i0, lane, s);
-    }
-};
-
-// --- the warp walker ------------------------------------------------------------
-// 32 steps of one (super-row, tile) block: after 32 rotations every j value is
-// back in its home lane.
-template <class P, int FLAGS, int MODE>
-__device__ __forceinline__ void run_tile(const PairArgs& A, const typename P::IState& is, typename P::JState& js,
-                                         typename P::Part& ip, int i0, int jbase, int lane, int next) {
-#pragma unroll 2
-    for (int k = 0; k < 32; ++k) {
-        const Mask m = step_mask<MODE>(k, lane);
-        P::template pair<FLAGS, MODE>(A, is, js, ip, m, i0, jbase, k);
-        P::rotate(js, next);
-    }
-}
-
-// Work of replica r is walked as super-rows K = 0 .. ceil(nb/2) - 1 (nb tiles
-// of 32 atoms), each over tiles J = 2K .. nb-1; a task is (replica, K, J,
-// number of tiles) and may continue into the next super-rows and replicas.
-template <class P, int FLAGS>
-__global__ void __launch_bounds__(256) k_pairs(PairArgs A, const int4* __restrict__ tasks, int n_tasks) {
+// MINB = 1 leaves the register count to the compiler; MINB = 3 caps it so that
+// three 256-thread blocks fit on an SM (more warps, a few spills).
+template <class P, int FLAGS, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_pairs(PairArgs A, const int4* __restrict__ tasks, int n_tasks) {
+    extern __shared__ long long s_acc[];
     const int lane = threadIdx.x & 31;
     const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (w >= n_tasks) return;
-    const int4 t = tasks[w];
-    int r = t.x, K = t.y, J = t.z;
-    const int cnt = t.w;
-    int64_t base = A.atom_off[r];
-    int n = (int)(A.atom_off[r + 1] - base);
-    int nb = (n + 31) >> 5;
-    int nk = (nb + 1) >> 1;
-    typename P::IState is;
-    P::load_i(A, base, n, 64 * K, lane, is);
-    const int next = (lane + 1) & 31;
-    for (int c = 0; c < cnt; ++c) {
-        typename P::JState js;
-        P::load_j(A, base, n, 32 * J + lane, js);
-        typename P::Part ip;
-        ip.zero();
-        if (J >= 2 * K + 2) run_tile<P, FLAGS, M_FULL>(A, is, js, ip, 64 * K, 32 * J, lane, next);
-        else if (J == 2 * K) run_tile<P, FLAGS, M_DX>(A, is, js, ip, 64 * K, 32 * J, lane, next);
-        else run_tile<P, FLAGS, M_DY>(A, is, js, ip, 64 * K, 32 * J, lane, next);
-        P::fold_i(is, ip);
-        P::flush_j(A, base, n, 32 * J + lane, js);
-        if (c + 1 < cnt && ++J == nb) {
-            P::flush_i(A, r, base, n, 64 * K, lane, is);
-            if (++K == nk) {
-                do {
-                    ++r;
-                    base = A.atom_off[r];
-                    n = (int)(A.atom_off[r + 1] - base);
-                    nb = (n + 31) >> 5;
-                } while (nb == 0);
-                nk = (nb + 1) >> 1;
-                K = 0;
-            }
-            J = 2 * K;
-            P::load_i(A, base, n, 64 * K, lane, is);
-        }
-    }
-    P::flush_i(A, r, base, n, 64 * K, lane, is);
+    walk_task<P, FLAGS>(A, tasks[w], s_acc + (threadIdx.x >> 5) * P::NQ * 64, lane);
+}
+
+__global__ void k_tile_boxes(PairArgs A, int M, int total_tiles) {
+    const int lane = threadIdx.x & 31;
+    const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (t >= total_tiles) return;
+    tile_box_warp(A, M, t, lane);
+}
+
+cudaError_t launch_tile_boxes(const PairArgs& a, int M, int total_tiles, cudaStream_t s) {
+    if (!a.boxes || total_tiles == 0) return cudaSuccess;
+    k_tile_boxes<<<(total_tiles + 7) / 8, 256, 0, s>>>(a, M, total_tiles);
+    return cudaGetLastError();
 }
 
 template <class P, int FLAGS>
 static cudaError_t go(const PairArgs& a, const TaskList& t, int wpb, cudaStream_t s) {
     if (t.n_tasks == 0) return cudaSuccess;
     const int blocks = (t.n_tasks + wpb - 1) / wpb;
-    k_pairs<P, FLAGS><<<blocks, 32 * wpb, 0, s>>>(a, t.d_tasks, t.n_tasks);
+    const size_t smem = (size_t)wpb * P::NQ * 64 * sizeof(long long);
+    if (t.min_blocks >= 3) k_pairs<P, FLAGS, 3><<<blocks, 32 * wpb, smem, s>>>(a, t.d_tasks, t.n_tasks);
+    else k_pairs<P, FLAGS, 1><<<blocks, 32 * wpb, smem, s>>>(a, t.d_tasks, t.n_tasks);
     return cudaGetLastError();
 }
 

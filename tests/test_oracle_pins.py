@@ -233,3 +233,11 @@ def test_restraint_forces_fd(orc, plain):
         xm[i, k] -= h
         fd = -(orc.restraints(xp)[0].sum() - orc.restraints(xm)[0].sum()) / (2 * h)
         assert fd == pytest.approx(F[i, k], abs=1e-5)
+
+
+def test_born_radii_subset_matches_full(orc):
+    b = synth.random_batch([300], seed=2, sites=False)
+    x, q, rho, scr, _ = orc.batch_arrays(b)
+    full = orc.born_radii(x, rho, scr)["R"]
+    idx = np.array([0, 5, 77, 299])
+    assert np.array_equal(orc.born_radii_subset(x, rho, scr, idx), full[idx])
