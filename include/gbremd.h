@@ -282,16 +282,17 @@ int gb_energy_forces_static(int32_t n_atoms, const gb_params* params, const floa
 int gb_set_profiling(gb_ctx* ctx, int32_t enable);
 int gb_pass_times(gb_ctx* ctx, double* mean_ms);
 
-/* MD driver kernel choice.  Enabled (when the device can hold the grid;
- * off by default): every run of MD steps up to the next Monte Carlo or
- * exchange point is ONE cooperative launch of a persistent kernel whose blocks stay
- * resident and pass the phases of each step (BAOAB halves, the three pair
- * passes, the O(N) transforms) through grid-wide barriers; a barrier that
- * waits too long records GB_ERR_TIMEOUT (see gb_sync_status) instead of
- * hanging.  Disabled: eight launches per step (the kernels gb_energy_forces
- * uses, the BAOAB halves and the tile bounding boxes).  With profiling on, gb_persist_times returns out[0] the mean ms per
- * MD step inside the persistent launches of the last block, out[1] the mean
- * ms per launch and out[2] the mean steps per launch. */
+/* MD driver kernel choice.  Enabled (off by default): every run of MD steps
+ * up to the next Monte Carlo or exchange point is ONE launch of a persistent
+ * kernel whose warps take the work of those steps -- BAOAB halves, the three
+ * pair passes, the O(N) transforms, replica by replica -- from a queue, each
+ * item waiting only for the items of the same replica it depends on, so the
+ * passes of different replicas overlap.  A wait that takes too long records
+ * GB_ERR_TIMEOUT (see gb_sync_status) instead of hanging.  Disabled: eight
+ * launches per step (the kernels gb_energy_forces uses, the BAOAB halves and
+ * the tile bounding boxes).  With profiling on, gb_persist_times returns
+ * out[0] the mean ms per MD step inside the persistent launches of the last
+ * block, out[1] the mean ms per launch and out[2] the mean steps per launch. */
 int gb_set_persistent(gb_ctx* ctx, int32_t enable);
 int gb_persist_times(gb_ctx* ctx, double* out);
 

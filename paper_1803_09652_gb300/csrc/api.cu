@@ -50,7 +50,11 @@ struct gb_ctx {
     int persist_grid = 0;
     bool use_persist = false;
     gbk::TaskList ptasks;
-    unsigned* bar = nullptr;
+    int* ptask_off = nullptr;           // [M+1]
+    int* phase_off = nullptr;           // [6][M+1]
+    int* phase_count = nullptr;         // [6][M]
+    int phase_base[7] = {0};
+    unsigned* qwords = nullptr;         // queue head + 6 x M completion counters
     std::vector<int> prof_steps_per_launch;
     // cached MD graph
     cudaGraphExec_t md_exec = nullptr;
@@ -141,8 +145,9 @@ int build_tasks_into(gb_ctx* c, int tpt, gbk::TaskList& out) {
 
 int build_tasks(gb_ctx* c) { return build_tasks_into(c, c->tpt, c->tasks); }
 
-// Resident grid of the persistent MD kernel and its task list: the batch's
-// work cut into one run per resident warp.
+// Tables of the persistent MD kernel: per-replica pair tasks (runs of `tpt`
+// tiles that never leave their replica), item offsets and counts of the six
+// phases.  The grid is sized to the resident capacity of the device.
 int setup_persist(gb_ctx* c) {
     int dev = 0, sms = 0, per_sm = 0;
     GB_CHECK(c, cudaGetDevice(&dev));
@@ -154,8 +159,49 @@ int setup_persist(gb_ctx* c) {
     }
     c->persist_grid = sms * per_sm;
     const int64_t warps = (int64_t)c->persist_grid * 4;
-    const int tpt = (int)std::max<int64_t>(1, (c->total_tiles + warps - 1) / warps);
-    return build_tasks_into(c, tpt, c->ptasks);
+    // about four pair items per resident warp and pass
+    const int tpt = (int)std::max<int64_t>(1, c->total_tiles / (4 * warps));
+    const int M = c->M;
+    std::vector<int4> t;
+    std::vector<int> toff(M + 1, 0), cnt(6 * M, 0), poff(6 * (M + 1), 0);
+    for (int r = 0; r < M; ++r) {
+        const int64_t n = c->off_h[r + 1] - c->off_h[r];
+        const int nb = (int)((n + 31) / 32), nk = (nb + 1) / 2;
+        int64_t left = gbk::pair_units(n);
+        int K = 0, J = 0;
+        while (left > 0) {
+            const int run = (int)std::min<int64_t>(tpt, left);
+            t.push_back(make_int4(r, K, J, run));
+            left -= run;
+            int64_t k = run;
+            while (k > 0 && K < nk) {
+                const int rowleft = nb - J;
+                if (k < rowleft) { J += (int)k; k = 0; }
+                else { k -= rowleft; ++K; J = 2 * K; }
+            }
+        }
+        toff[r + 1] = (int)t.size();
+        const int tasks_r = toff[r + 1] - toff[r];
+        const int per_phase[6] = {nb, tasks_r, nb, tasks_r, nb, tasks_r};
+        for (int p = 0; p < 6; ++p) cnt[p * M + r] = per_phase[p];
+    }
+    c->phase_base[0] = 0;
+    for (int p = 0; p < 6; ++p) {
+        for (int r = 0; r < M; ++r) poff[p * (M + 1) + r + 1] = poff[p * (M + 1) + r] + cnt[p * M + r];
+        c->phase_base[p + 1] = c->phase_base[p] + poff[p * (M + 1) + M];
+    }
+    if (c->ptasks.d_tasks) cudaFree(c->ptasks.d_tasks);
+    c->ptasks.n_tasks = (int)t.size();
+    GB_CHECK(c, zalloc(&c->ptasks.d_tasks, t.size()));
+    GB_CHECK(c, cudaMemcpy(c->ptasks.d_tasks, t.data(), t.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    GB_CHECK(c, zalloc(&c->ptask_off, M + 1));
+    GB_CHECK(c, cudaMemcpy(c->ptask_off, toff.data(), sizeof(int) * (M + 1), cudaMemcpyHostToDevice));
+    GB_CHECK(c, zalloc(&c->phase_count, 6 * (size_t)M));
+    GB_CHECK(c, cudaMemcpy(c->phase_count, cnt.data(), sizeof(int) * 6 * M, cudaMemcpyHostToDevice));
+    GB_CHECK(c, zalloc(&c->phase_off, 6 * (size_t)(M + 1)));
+    GB_CHECK(c, cudaMemcpy(c->phase_off, poff.data(), sizeof(int) * 6 * (M + 1), cudaMemcpyHostToDevice));
+    GB_CHECK(c, zalloc(&c->qwords, 1 + 6 * (size_t)M));
+    return GB_OK;
 }
 
 int default_tpt(const gb_ctx* c) {
@@ -305,7 +351,7 @@ extern "C" int gb_ctx_create(gb_ctx** out, int32_t n_rep, const int64_t* atom_of
     step(zalloc(&c->cfac, N));
     step(zalloc(&c->cc, N));
     step(zalloc(&c->err, 1));
-    step(zalloc(&c->bar, 2));
+
     c->mc_parts = (c->max_n + gbk::MC_CHUNK - 1) / gbk::MC_CHUNK;
     {
         std::vector<int> toff(n_rep + 1, 0);
@@ -346,7 +392,10 @@ extern "C" int gb_ctx_destroy(gb_ctx* c) {
     for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     cudaFree(c->tasks.d_tasks);
     cudaFree(c->ptasks.d_tasks);
-    cudaFree(c->bar);
+    cudaFree(c->ptask_off);
+    cudaFree(c->phase_off);
+    cudaFree(c->phase_count);
+    cudaFree(c->qwords);
     cudaFree(c->off_d);
     cudaFree(c->I_acc);
     cudaFree(c->dR_acc);
@@ -659,11 +708,14 @@ int enqueue_steps(gb_ctx* c, gb_md_state* st, const gb_sites* sites, int64_t len
         a.aa = aa;
         a.md = m;
         a.tasks = c->ptasks.d_tasks;
-        a.n_tasks = c->ptasks.n_tasks;
+        a.task_off = c->ptask_off;
+        a.phase_off = c->phase_off;
+        a.count = c->phase_count;
+        for (int p = 0; p < 7; ++p) a.phase_base[p] = c->phase_base[p];
         a.M = c->M;
-        a.total_tiles = c->n_tiles32;
         a.R_out = st->R;
-        a.bar = c->bar;
+        a.head = c->qwords;
+        a.done = c->qwords + 1;
         a.err = c->err;
         if (c->prof) {
             int rc = ensure_prof_events(c, len);

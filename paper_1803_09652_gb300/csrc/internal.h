@@ -181,19 +181,22 @@ struct GridExArgs {
 cudaError_t launch_grid_exchange(const GridExArgs& a, cudaStream_t s);
 
 // Persistent MD kernel (persist.cu): nsteps MD steps of the whole batch in one
-// cooperative launch.
+// launch, as a queue of warp items with per-(phase, replica) completion counts.
 struct PersistArgs {
     PairArgs pa;
     AtomArgs aa;
     MDArgs md;
-    const int4* tasks;         // one task per resident warp (or fewer)
-    int n_tasks;
+    const int4* tasks;         // pair tasks of every replica, replica after replica
+    const int* task_off;       // [M+1] first task of each replica
+    const int* phase_off;      // [6][M+1] first item of each replica within a phase
+    const int* count;          // [6][M] items of each replica per phase
+    int phase_base[7];         // first item of each phase within a step; [6] = items per step
     int M;
-    int total_tiles;           // 32-atom tiles of the batch
     int nsteps;                // MD steps in this launch
     int step0;                 // index of the first of them in the enqueued block
     float* R_out;              // Born radii of the last step (nullable)
-    unsigned* bar;             // [2] barrier words, cleared by launch_persist
+    unsigned* head;            // queue head, followed by the 6 x M completion counters
+    unsigned* done;
     int* err;
 };
 size_t persist_smem();

@@ -1,25 +1,28 @@
-// Persistent MD kernel: all phases of several BAOAB steps of the whole batch in
-// one cooperative launch, separated by grid-wide barriers.
+// Persistent MD kernel: several BAOAB steps of the whole batch in one launch,
+// scheduled as a stream of warp-sized work items with per-replica
+// dependencies instead of global barriers.
 //
-// The three pair passes of a small batch (8 x 2048 atoms: ~40 us each) lose a
-// large share of their time to launch, ramp-up and tail; here every block
-// stays resident for the whole launch and the phases of a step are
-//   A  second half of the previous step (total force -> kick), first half of
-//      this step (B A O A), bounding boxes of the moved tiles   [warp per tile]
-//   1  Born integrals                                          [warp tasks]
-//   2  Born radii                                              [thread per atom]
-//   3  GB + Coulomb forces, dE/dR, soft repulsion              [warp tasks]
-//   4  chain factors, chain bonds                              [thread per atom]
-//   5  Born chain-rule forces                                  [warp tasks]
-// with a barrier after each.  The last step ends with the second half only
-// and stores the forces for the next launch.  Monte Carlo attempts and
-// exchanges run between launches.
+// Each MD step s of replica r runs six phases:
+//   0  close step s-1 (total force -> kick), open step s (B A O A), rebuild
+//      the tile's bounding box                              [item: 32-atom tile]
+//   1  Born integrals                                       [item: pair task]
+//   2  Born radii                                           [item: 32 atoms]
+//   3  GB + Coulomb forces, dE/dR, soft repulsion           [item: pair task]
+//   4  chain factors, chain bonds                           [item: 32 atoms]
+//   5  Born chain-rule forces                               [item: pair task]
+// and the launch ends with phase 0 of step nsteps (kick only; the forces are
+// stored for the next launch).  Items are numbered step-major, then
+// phase-major, then replica-major, and warps take them in that order from a
+// global counter.  Phase p > 0 of (s, r) waits until all phase p-1 items of
+// (s, r) are done, phase 0 of (s, r) until all phase 5 items of (s-1, r) are
+// done.  Every wait is on items that come earlier in the order, which some
+// running warp has already taken and will finish, so the schedule cannot
+// deadlock and needs no co-residency.  While the last replica of a pass is
+// still finishing, other warps already work on the next pass of the first
+// replicas: the pass tails of a small batch overlap.
 //
-// Barrier: one arrival counter and one release word, both cleared before the
-// launch.  Waits are bounded: after SPIN_LIMIT polls a block records
-// GB_ERR_TIMEOUT and every block leaves the kernel at its next barrier.  The
-// launch is cooperative, so all blocks are co-resident and the limit is never
-// reached in correct operation.
+// Waits are bounded: after SPIN_LIMIT polls the warp records GB_ERR_TIMEOUT and
+// stops taking work; the others then time out on it and stop too.
 #include "atoms_impl.cuh"
 #include "pairs_impl.cuh"
 
@@ -35,97 +38,79 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     return v;
 }
 
-// Returns false (in every thread of the block) when the kernel must stop.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& epoch, int* err) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ++epoch;
-        __threadfence();
-        const unsigned arrived = atomicAdd(&bar[0], 1u) + 1u;
-        int ok = 1;
-        if (arrived == gridDim.x * epoch) {
-            __threadfence();
-            atomicExch(&bar[1], epoch);
-        } else {
-            unsigned it = 0;
-            while (ld_acquire(&bar[1]) < epoch) {
-                if (++it > SPIN_LIMIT) {
-                    atomicCAS(err, 0, GB_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(32);
+// Lane 0 waits until *ctr >= target; returns false when the wait gave up or
+// another warp reported an error.
+__device__ __forceinline__ bool wait_count(const unsigned* ctr, unsigned target, int* err, int lane) {
+    int ok = 1;
+    if (lane == 0) {
+        unsigned it = 0;
+        while (ld_acquire(ctr) < target) {
+            if (*(volatile int*)err != 0) { ok = 0; break; }
+            if (++it > SPIN_LIMIT) {
+                atomicCAS(err, 0, GB_ERR_TIMEOUT);
+                ok = 0;
+                break;
             }
+            __nanosleep(64);
         }
-        __threadfence();
-        s_ok = ok && (*(volatile int*)err == 0);
     }
-    __syncthreads();
-    return s_ok != 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+    return ok != 0;
 }
 
-__device__ __forceinline__ int replica_of_tile(const PairArgs& A, int M, int t) {
-    int lo = 0, hi = M;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (A.tile_off[mid] <= t) lo = mid;
-        else hi = mid;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ int replica_of_atom(const AtomArgs& A, int M, int64_t g) {
-    int lo = 0, hi = M;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (A.atom_off[mid] <= g) lo = mid;
-        else hi = mid;
-    }
-    return lo;
-}
-
-// Phase A over the tiles owned by this warp.  second: close the previous step
-// (force from the accumulators, kick).  s_first >= 0: open step s_first
-// (B A O A with the same force) and rebuild the tile's box; otherwise store
-// the force for the next launch.
-__device__ __forceinline__ void phase_halfsteps(const PersistArgs& P, int gw, int W, int lane, bool second,
-                                                int s_first) {
+// Phase 0 on tile u of replica r.  second: close the previous step (force
+// from the accumulators, kick).  first: open step `step` (B A O A with the
+// same force) and rebuild the tile's box; otherwise store the force.
+__device__ __forceinline__ void tile_halfsteps(const PersistArgs& P, int r, int u, int lane, bool second,
+                                               bool first, u64 step) {
     const MDArgs& m = P.md;
     const int64_t N = P.pa.N;
-    for (int t = gw; t < P.total_tiles; t += W) {
-        const int r = replica_of_tile(P.pa, P.M, t);
-        const int64_t base = P.pa.atom_off[r];
-        const int n = (int)(P.pa.atom_off[r + 1] - base);
-        const int i = 32 * (t - P.pa.tile_off[r]) + lane;
-        if (i < n) {
-            const int64_t g = base + i;
-            float4 v = __ldcg(&m.vel[g]);
-            float4 f;
-            if (second) {
-                f = make_float4((float)unfix(__ldcg(&P.aa.F_acc[g])), (float)unfix(__ldcg(&P.aa.F_acc[N + g])),
-                                (float)unfix(__ldcg(&P.aa.F_acc[2 * N + g])), 0.0f);
-                P.aa.F_acc[g] = 0;
-                P.aa.F_acc[N + g] = 0;
-                P.aa.F_acc[2 * N + g] = 0;
-                v.x = fmaf(m.h * m.inv_m, f.x, v.x);
-                v.y = fmaf(m.h * m.inv_m, f.y, v.y);
-                v.z = fmaf(m.h * m.inv_m, f.z, v.z);
-            } else {
-                f = __ldcg(&m.force[g]);
-            }
-            if (s_first >= 0) {
-                float4 x = __ldcg(&m.xyzq[g]);
-                const u64 step = __ldcg(&m.ctr[0]) + (u64)(P.step0 + s_first) + 1;
-                baoab_first(m, x, v, f, md_normals(m.seed, (u64)r, step, (u64)i));
-                m.xyzq[g] = x;
-            } else {
-                m.force[g] = f;
-            }
-            m.vel[g] = v;
+    const int64_t base = P.pa.atom_off[r];
+    const int n = (int)(P.pa.atom_off[r + 1] - base);
+    const int i = 32 * u + lane;
+    if (i < n) {
+        const int64_t g = base + i;
+        float4 v = __ldcg(&m.vel[g]);
+        float4 f;
+        if (second) {
+            f = make_float4((float)unfix(__ldcg(&P.aa.F_acc[g])), (float)unfix(__ldcg(&P.aa.F_acc[N + g])),
+                            (float)unfix(__ldcg(&P.aa.F_acc[2 * N + g])), 0.0f);
+            P.aa.F_acc[g] = 0;
+            P.aa.F_acc[N + g] = 0;
+            P.aa.F_acc[2 * N + g] = 0;
+            v.x = fmaf(m.h * m.inv_m, f.x, v.x);
+            v.y = fmaf(m.h * m.inv_m, f.y, v.y);
+            v.z = fmaf(m.h * m.inv_m, f.z, v.z);
+        } else {
+            f = __ldcg(&m.force[g]);
         }
-        if (s_first >= 0) tile_box_warp(P.pa, P.M, t, lane);
+        if (first) {
+            float4 x = __ldcg(&m.xyzq[g]);
+            baoab_first(m, x, v, f, md_normals(m.seed, (u64)r, step, (u64)i));
+            m.xyzq[g] = x;
+        } else {
+            m.force[g] = f;
+        }
+        m.vel[g] = v;
     }
+    if (first) tile_box_warp(P.pa, P.M, P.pa.tile_off[r] + u, lane);
+}
+
+// Phase 4 on atoms 32u .. 32u+31 of replica r: chain factor, chain bonds.
+__device__ __forceinline__ void atoms_chain_bonds(const PersistArgs& P, int r, int u, int lane) {
+    const int64_t N = P.pa.N;
+    const int64_t base = P.pa.atom_off[r];
+    const int n = (int)(P.pa.atom_off[r + 1] - base);
+    const int i = 32 * u + lane;
+    if (i >= n) return;
+    const int64_t g = base + i;
+    double R;
+    chain_factor_atom(P.aa, g, &R);
+    const float3 fb = bond_force(P.md, P.md.xyzq, base, i, n);
+    P.aa.F_acc[g] = __ldcg(&P.aa.F_acc[g]) + (u64)fix(fb.x);
+    P.aa.F_acc[N + g] = __ldcg(&P.aa.F_acc[N + g]) + (u64)fix(fb.y);
+    P.aa.F_acc[2 * N + g] = __ldcg(&P.aa.F_acc[2 * N + g]) + (u64)fix(fb.z);
 }
 
 template <int REP>
@@ -133,39 +118,53 @@ __global__ void __launch_bounds__(PERSIST_THREADS, 6) k_md_persist(PersistArgs P
     extern __shared__ long long s_acc[];
     constexpr int EFL = REP ? EF_REP : 0;
     const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
-    const int W = gridDim.x * (blockDim.x >> 5);
-    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t T = (int64_t)gridDim.x * blockDim.x;
-    long long* sa = s_acc + wib * PERSIST_NQ * 64;
-    const int64_t N = P.pa.N;
-    unsigned epoch = 0;
-
-    phase_halfsteps(P, gw, W, lane, false, 0);
-    for (int s = 0; s < P.nsteps; ++s) {
-        if (!grid_barrier(P.bar, epoch, P.err)) return;
-        for (int t = gw; t < P.n_tasks; t += W) walk_task<Born, 0>(P.pa, P.tasks[t], sa, lane);
-        if (!grid_barrier(P.bar, epoch, P.err)) return;
-        for (int64_t g = gt; g < N; g += T) born_finalize_atom(P.aa, g, P.R_out);
-        if (!grid_barrier(P.bar, epoch, P.err)) return;
-        for (int t = gw; t < P.n_tasks; t += W) walk_task<EnergyF<EFL>, EFL>(P.pa, P.tasks[t], sa, lane);
-        if (!grid_barrier(P.bar, epoch, P.err)) return;
-        for (int64_t g = gt; g < N; g += T) {
-            double R;
-            chain_factor_atom(P.aa, g, &R);
-            const int r = replica_of_atom(P.aa, P.M, g);
-            const int64_t base = P.aa.atom_off[r];
-            const int n = (int)(P.aa.atom_off[r + 1] - base);
-            const float3 fb = bond_force(P.md, P.md.xyzq, base, (int)(g - base), n);
-            P.aa.F_acc[g] = __ldcg(&P.aa.F_acc[g]) + (u64)fix(fb.x);
-            P.aa.F_acc[N + g] = __ldcg(&P.aa.F_acc[N + g]) + (u64)fix(fb.y);
-            P.aa.F_acc[2 * N + g] = __ldcg(&P.aa.F_acc[2 * N + g]) + (u64)fix(fb.z);
+    long long* sa = s_acc + (threadIdx.x >> 5) * PERSIST_NQ * 64;
+    const unsigned per_step = (unsigned)P.phase_base[6];
+    const unsigned total = per_step * (unsigned)P.nsteps + (unsigned)P.phase_base[1];
+    const u64 step0 = __ldcg(&P.md.ctr[0]) + (u64)P.step0;
+    for (;;) {
+        unsigned item = 0;
+        if (lane == 0) item = atomicAdd(P.head, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= total) break;
+        const int s = (int)(item / per_step);
+        const unsigned rem = item - (unsigned)s * per_step;
+        int p = 0;
+        while (p < 5 && rem >= (unsigned)P.phase_base[p + 1]) ++p;
+        const int* off = P.phase_off + p * (P.M + 1);
+        const int x = (int)(rem - (unsigned)P.phase_base[p]);
+        int lo = 0, hi = P.M;                  // replica with off[lo] <= x < off[lo + 1]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (off[mid] <= x) lo = mid;
+            else hi = mid;
         }
-        if (!grid_barrier(P.bar, epoch, P.err)) return;
-        for (int t = gw; t < P.n_tasks; t += W) walk_task<Chain, 0>(P.pa, P.tasks[t], sa, lane);
-        if (!grid_barrier(P.bar, epoch, P.err)) return;
-        phase_halfsteps(P, gw, W, lane, true, s + 1 < P.nsteps ? s + 1 : -1);
+        const int r = lo, u = x - off[r];
+        // dependency: the previous phase of (s, r) -- or phase 5 of (s-1, r)
+        bool ok = true;
+        if (p > 0) {
+            ok = wait_count(&P.done[(p - 1) * P.M + r], (unsigned)(s + 1) * (unsigned)P.count[(p - 1) * P.M + r],
+                            P.err, lane);
+        } else if (s > 0) {
+            ok = wait_count(&P.done[5 * P.M + r], (unsigned)s * (unsigned)P.count[5 * P.M + r], P.err, lane);
+        }
+        if (!ok) break;
+        switch (p) {
+            case 0: tile_halfsteps(P, r, u, lane, s > 0, s < P.nsteps, step0 + (u64)s + 1); break;
+            case 1: walk_task<Born, 0>(P.pa, P.tasks[P.task_off[r] + u], sa, lane); break;
+            case 2: {
+                const int64_t base = P.pa.atom_off[r];
+                const int i = 32 * u + lane;
+                if (i < (int)(P.pa.atom_off[r + 1] - base)) born_finalize_atom(P.aa, base + i, P.R_out);
+                break;
+            }
+            case 3: walk_task<EnergyF<EFL>, EFL>(P.pa, P.tasks[P.task_off[r] + u], sa, lane); break;
+            case 4: atoms_chain_bonds(P, r, u, lane); break;
+            default: walk_task<Chain, 0>(P.pa, P.tasks[P.task_off[r] + u], sa, lane); break;
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) atomicAdd(&P.done[p * P.M + r], 1u);
     }
 }
 
@@ -178,20 +177,13 @@ cudaError_t persist_occupancy(int rep, int* blocks_per_sm) {
 }
 
 cudaError_t launch_persist(const PersistArgs& a, int rep, int grid, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), s);
+    // queue head and the per-(phase, replica) completion counters start at zero
+    cudaError_t e = cudaMemsetAsync(a.head, 0, sizeof(unsigned) * (1 + 6 * (size_t)a.M), s);
     if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(PERSIST_THREADS);
-    cfg.dynamicSmemBytes = persist_smem();
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    if (rep) return cudaLaunchKernelEx(&cfg, k_md_persist<1>, a);
-    return cudaLaunchKernelEx(&cfg, k_md_persist<0>, a);
+    const size_t smem = persist_smem();
+    if (rep) k_md_persist<1><<<grid, PERSIST_THREADS, smem, s>>>(a);
+    else k_md_persist<0><<<grid, PERSIST_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace gbk

@@ -19,11 +19,12 @@ def pkg():
     return p
 
 
-def _setup(pkg, b, seed, mc_every=0, ex_every=0, with_sites=False):
+def _setup(pkg, b, seed, mc_every=0, ex_every=0, with_sites=False, persistent=False):
     import torch
     dev = device()
     params = pkg.default_params(rep_k=10.0, rep_sigma=2.5)
     ctx = pkg.Context(b.atom_off, params)
+    ctx.set_persistent(persistent)
     N, M = b.n_atoms, b.n_rep
     S = dict(xyzq=torch.as_tensor(b.xyzq(), device=dev),
              rad=torch.as_tensor(b.rad_screen(), device=dev),
@@ -53,10 +54,11 @@ def _setup(pkg, b, seed, mc_every=0, ex_every=0, with_sites=False):
     return ctx, st, S, sites
 
 
-def test_one_baoab_step_matches_oracle(pkg):
+@pytest.mark.parametrize("persistent", [False, True])
+def test_one_baoab_step_matches_oracle(pkg, persistent):
     import torch
     b = synth.random_batch([120, 64, 33], seed=3, sites=False)
-    ctx, st, S, _ = _setup(pkg, b, seed=5)
+    ctx, st, S, _ = _setup(pkg, b, seed=5, persistent=persistent)
     torch.cuda.synchronize()
     x, q, rho, scr, off = oracle.batch_arrays(b)
     p = oracle_params(rep_k=10.0, rep_sigma=2.5)
@@ -73,11 +75,14 @@ def test_one_baoab_step_matches_oracle(pkg):
     assert st.step == 1
 
 
-def test_graph_replay_equals_direct_launches(pkg):
+@pytest.mark.parametrize("persistent", [False, True])
+def test_graph_replay_equals_direct_launches(pkg, persistent):
     import torch
     b = synth.config_eremd(4, 300)
-    ctx1, st1, S1, sites1 = _setup(pkg, b, seed=8, mc_every=10, ex_every=50, with_sites=True)
-    ctx2, st2, S2, sites2 = _setup(pkg, b, seed=8, mc_every=10, ex_every=50, with_sites=True)
+    ctx1, st1, S1, sites1 = _setup(pkg, b, seed=8, mc_every=10, ex_every=50, with_sites=True,
+                                   persistent=persistent)
+    ctx2, st2, S2, sites2 = _setup(pkg, b, seed=8, mc_every=10, ex_every=50, with_sites=True,
+                                   persistent=persistent)
     ctx1.md_segment(st1, sites1, 100)           # two captured blocks of 50
     for _ in range(100):
         ctx2.md_segment(st2, sites2, 1)         # direct launches
@@ -89,10 +94,12 @@ def test_graph_replay_equals_direct_launches(pkg):
     assert st1.step == st2.step == 100 and st1.attempt == st2.attempt == 2
 
 
-def test_eremd_segment_bookkeeping(pkg):
+@pytest.mark.parametrize("persistent", [False, True])
+def test_eremd_segment_bookkeeping(pkg, persistent):
     import torch
     b = synth.config_eremd(8, 256)
-    ctx, st, S, sites = _setup(pkg, b, seed=11, mc_every=10, ex_every=20, with_sites=True)
+    ctx, st, S, sites = _setup(pkg, b, seed=11, mc_every=10, ex_every=20, with_sites=True,
+                               persistent=persistent)
     ctx.md_segment(st, sites, 400)
     torch.cuda.synchronize()
     ctx.sync_status()
@@ -115,3 +122,19 @@ def test_eremd_segment_bookkeeping(pkg):
         qo = tables["site_q_off"][s] + st_h[s] * na
         assert np.array_equal(x[idx, 3], tables["q_state"][qo:qo + na])
     assert st.attempt == 20
+
+
+def test_persistent_driver_tracks_three_pass_driver(pkg):
+    """Same trajectory start, both drivers: positions agree to FP32 rounding
+    after 20 steps (they differ only in where the bond forces are rounded)."""
+    import torch
+    b = synth.random_batch([300, 257, 64, 1], seed=13, sites=False)
+    c1, st1, S1, _ = _setup(pkg, b, seed=4, persistent=False)
+    c2, st2, S2, _ = _setup(pkg, b, seed=4, persistent=True)
+    c1.md_segment(st1, None, 20)
+    c2.md_segment(st2, None, 20)
+    torch.cuda.synchronize()
+    c1.sync_status()
+    c2.sync_status()
+    d = (S1["xyzq"] - S2["xyzq"]).abs().max().item()
+    assert d < 1e-3, d
