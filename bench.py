@@ -404,19 +404,40 @@ def main():
         torch.distributed.destroy_process_group()
 
 
+PAIR_SOURCES = ("pairs_impl.cuh", "pairs.cu", "poly_coeffs.h", "common.cuh")
+
+
+def pair_source_hash():
+    """First 16 hex digits of the sha256 of the pair-kernel sources."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in PAIR_SOURCES:
+        with open(os.path.join(ROOT, "paper_1803_09652_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def read_traffic(name):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if any."""
+    """DRAM bytes per launch of `name` from the committed ncu summary; None when
+    there is none or the pair-kernel sources changed since it was captured."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path):
         return None
+    table, src = {}, None
     for line in open(path):
         parts = line.split()
-        if len(parts) >= 2 and parts[0] == name:
-            try:
-                return float(parts[1])
-            except ValueError:
-                return None
-    return None
+        if len(parts) < 2 or parts[0].startswith("#"):
+            continue
+        if parts[0] == "sources":
+            src = parts[1]
+            continue
+        try:
+            table[parts[0]] = float(parts[1])
+        except ValueError:
+            pass
+    if src != pair_source_hash():
+        return None
+    return table.get(name)
 
 
 def plain_form(pkg, b, dev, params, n_bench):
