@@ -380,7 +380,8 @@ def main():
                        "atoms_per_replica": N_ATOMS, "md_steps_per_step": MD_PER_STEP,
                        "mc_every": MC_EVERY, "exchange_every": EX_EVERY,
                        "pairs_per_md_step": pairs_md, "l2": "flushed between steps (256 MB write)",
-                       "tiles": list(S.ctx.tiles()), "parallelism": "replicas batched on one GPU"},
+                       "tiles": list(S.ctx.tiles()), "reg_caps": list(S.ctx.reg_caps()),
+                       "parallelism": "replicas batched on one GPU"},
             "replica_md_steps_per_s": rep_steps,
             "kernel_timing": timing,
             "fp32_flops_per_pair": FLOPS_PER_PAIR,

@@ -90,9 +90,14 @@ int gb_sync_status(gb_ctx* ctx, void* stream);
  * the given inputs and keeps the fastest; gb_set_tiles forces one. */
 int gb_autotune(gb_ctx* ctx, const float* xyzq, const float* rad_screen, void* stream);
 int gb_set_tiles(gb_ctx* ctx, int32_t warps_per_block, int32_t tiles_per_task);
-/* Register cap of the pair kernels: 1 = the compiler's choice, 3 = at most
- * ~85 registers per thread so that three 256-thread blocks fit per SM. */
-int gb_set_reg_cap(gb_ctx* ctx, int32_t min_blocks_per_sm);
+/* Register cap of the pair kernel of one pass (0 Born radii, 1 energy and
+ * direct forces, 2 Born chain rule; -1 = all three), as 256-thread blocks
+ * per SM: 1 = the compiler's choice, 3 = at most 80 registers per thread,
+ * 4 = at most 64 (more resident warps, more spills).  gb_autotune picks
+ * each pass's cap; the default is 3.  GB_ERR_INVALID_ARG for other values. */
+int gb_set_reg_cap(gb_ctx* ctx, int32_t pass, int32_t min_blocks_per_sm);
+/* The three caps in pass order into caps[3] (host memory). */
+int gb_get_reg_caps(const gb_ctx* ctx, int32_t* caps);
 int gb_get_tiles(const gb_ctx* ctx, int32_t* warps_per_block, int32_t* tiles_per_task);
 
 /* Effective Born radii of every atom (OBC model, Sec. III.D):

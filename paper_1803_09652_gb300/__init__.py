@@ -103,7 +103,8 @@ def load(path: Optional[str] = None):
         "gb_sync_status": [_P, _P],
         "gb_autotune": [_P, _P, _P, _P],
         "gb_set_tiles": [_P, i32, i32],
-        "gb_set_reg_cap": [_P, i32],
+        "gb_set_reg_cap": [_P, i32, i32],
+        "gb_get_reg_caps": [_P, _P],
         "gb_get_tiles": [_P, C.POINTER(i32), C.POINTER(i32)],
         "gb_born_radii": [_P, _P, _P, _P, _P],
         "gb_energy_forces": [_P, _P, _P, _P, _P, _P, _P, _P, _P],
@@ -252,8 +253,15 @@ class Context:
     def set_tiles(self, warps_per_block: int, tiles_per_task: int):
         _check(self.lib.gb_set_tiles(self.h, warps_per_block, tiles_per_task), self.h)
 
-    def set_reg_cap(self, min_blocks: int):
-        _check(self.lib.gb_set_reg_cap(self.h, int(min_blocks)), self.h)
+    def set_reg_cap(self, min_blocks: int, pass_index: int = -1):
+        """Register cap (1, 3 or 4 blocks of 256 threads per SM) of one pair
+        pass (0 Born, 1 energy, 2 chain) or of all three (-1)."""
+        _check(self.lib.gb_set_reg_cap(self.h, int(pass_index), int(min_blocks)), self.h)
+
+    def reg_caps(self):
+        caps = (C.c_int32 * 3)()
+        _check(self.lib.gb_get_reg_caps(self.h, caps), self.h)
+        return tuple(caps)
 
     def tiles(self):
         w, t = C.c_int32(), C.c_int32()

@@ -134,6 +134,14 @@ int build_tasks_into(gb_ctx* c, int tpt, gbk::TaskList& out) {
             }
         }
     }
+    // Costly blocks first: those at and next to a super-row's diagonal hold the
+    // chain's near pairs (closed forms, no far-block shortcut), so starting
+    // them early leaves the cheap far blocks for the end of the pass, where
+    // they even out the finishing times of the SMs.  Any order gives the same
+    // fixed-point sums.
+    std::stable_sort(t.begin(), t.end(), [](const int4& a, const int4& b) {
+        return a.z - 2 * a.y < b.z - 2 * b.y;
+    });
     if (out.d_tasks) cudaFree(out.d_tasks);
     out.d_tasks = nullptr;
     out.n_tasks = (int)t.size();
@@ -373,7 +381,7 @@ extern "C" int gb_ctx_create(gb_ctx** out, int32_t n_rep, const int64_t* atom_of
         return code;
     }
     c->tpt = default_tpt(c);
-    c->tasks.min_blocks = 3;
+    for (int k = 0; k < 3; ++k) c->tasks.cap[k] = 3;
     int rc = build_tasks(c);
     if (rc == GB_OK) rc = setup_persist(c);
     if (rc != GB_OK) {
@@ -448,11 +456,20 @@ extern "C" int gb_set_tiles(gb_ctx* c, int32_t wpb, int32_t tpt) {
     return GB_OK;
 }
 
-extern "C" int gb_set_reg_cap(gb_ctx* c, int32_t min_blocks) {
+extern "C" int gb_set_reg_cap(gb_ctx* c, int32_t pass, int32_t min_blocks) {
     if (!c) return fail(nullptr, GB_ERR_INVALID_ARG, "NULL context");
-    if (min_blocks != 1 && min_blocks != 3) return fail(c, GB_ERR_INVALID_ARG, "min_blocks must be 1 or 3");
-    c->tasks.min_blocks = min_blocks;
+    if (pass < -1 || pass > 2) return fail(c, GB_ERR_INVALID_ARG, "pass must be -1, 0, 1 or 2");
+    if (min_blocks != 1 && min_blocks != 3 && min_blocks != 4)
+        return fail(c, GB_ERR_INVALID_ARG, "min_blocks must be 1, 3 or 4");
+    for (int k = 0; k < 3; ++k)
+        if (pass < 0 || pass == k) c->tasks.cap[k] = min_blocks;
     if (c->md_exec) { cudaGraphExecDestroy(c->md_exec); c->md_exec = nullptr; c->md_key.clear(); }
+    return GB_OK;
+}
+
+extern "C" int gb_get_reg_caps(const gb_ctx* c, int32_t* caps) {
+    if (!c || !caps) return GB_ERR_INVALID_ARG;
+    for (int k = 0; k < 3; ++k) caps[k] = c->tasks.cap[k];
     return GB_OK;
 }
 
@@ -873,52 +890,69 @@ extern "C" int gb_md_segment(gb_ctx* c, gb_md_state* st, const gb_sites* sites, 
 // Autotuner: time one full force evaluation per candidate tile shape.
 
 extern "C" int gb_autotune(gb_ctx* c, const float* xyzq, const float* rad, void* stream) {
+    // Every (warps per block, tiles per task) candidate runs full evaluations
+    // with each register cap; the passes are timed one by one, so each pass
+    // keeps its own best cap and a candidate scores the sum of its passes' best.
     int rc = check_inputs(c, xyzq, rad);
     if (rc) return rc;
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     GB_CHECK(c, cudaStreamSynchronize(s));
     const int wpbs[] = {4, 8};
+    const int caps[] = {1, 3, 4};
     std::vector<int> tpts;
     const int base = default_tpt(c);
     for (int f : {1, 2, 4, 8, 16}) {
         int t = std::max(1, base * f / 4);
         if (std::find(tpts.begin(), tpts.end(), t) == tpts.end()) tpts.push_back(t);
     }
-    cudaEvent_t e0, e1;
-    GB_CHECK(c, cudaEventCreate(&e0));
-    GB_CHECK(c, cudaEventCreate(&e1));
+    cudaEvent_t ev[6];
+    for (auto& e : ev) GB_CHECK(c, cudaEventCreate(&e));
     float best = 1e30f;
-    int best_w = c->wpb, best_t = c->tpt, best_m = c->tasks.min_blocks;
+    int best_w = c->wpb, best_t = c->tpt, best_cap[3] = {c->tasks.cap[0], c->tasks.cap[1], c->tasks.cap[2]};
     for (int t : tpts) {
         rc = gb_set_tiles(c, c->wpb, t);
         if (rc) break;
-        for (int cfg = 0; cfg < 4; ++cfg) {
-            const int w = wpbs[cfg & 1];
+        for (int w : wpbs) {
             c->wpb = w;
-            c->tasks.min_blocks = (cfg & 2) ? 3 : 1;
-            float ms_min = 1e30f;
-            for (int rep = 0; rep < 3; ++rep) {
-                cudaEventRecord(e0, s);
-                rc = evaluate(c, xyzq, rad, nullptr, 0, nullptr, s);
+            float pass_best[3] = {1e30f, 1e30f, 1e30f};
+            int pass_cap[3] = {3, 3, 3};
+            for (int cap : caps) {
+                for (int k = 0; k < 3; ++k) c->tasks.cap[k] = cap;
+                float ms_min[3] = {1e30f, 1e30f, 1e30f};
+                for (int rep = 0; rep < 3 && !rc; ++rep) {
+                    rc = evaluate(c, xyzq, rad, nullptr, 0, nullptr, s, ev);
+                    if (rc) break;
+                    cudaEventSynchronize(ev[5]);
+                    float ms[3] = {0, 0, 0};
+                    cudaEventElapsedTime(&ms[0], ev[0], ev[1]);
+                    cudaEventElapsedTime(&ms[1], ev[2], ev[3]);
+                    cudaEventElapsedTime(&ms[2], ev[4], ev[5]);
+                    if (rep > 0)
+                        for (int k = 0; k < 3; ++k) ms_min[k] = std::min(ms_min[k], ms[k]);
+                }
                 if (rc) break;
-                rc = gbk::launch_forces_out(atom_args(c, xyzq, rad), nullptr, nullptr, nullptr, s) ==
-                             cudaSuccess ? GB_OK : GB_ERR_CUDA;
-                cudaEventRecord(e1, s);
-                cudaEventSynchronize(e1);
-                float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (rep > 0) ms_min = std::min(ms_min, ms);
+                for (int k = 0; k < 3; ++k)
+                    if (ms_min[k] < pass_best[k]) { pass_best[k] = ms_min[k]; pass_cap[k] = cap; }
             }
             if (rc) break;
-            if (ms_min < best) { best = ms_min; best_w = w; best_t = t; best_m = c->tasks.min_blocks; }
+            const float total = pass_best[0] + pass_best[1] + pass_best[2];
+            if (total < best) {
+                best = total;
+                best_w = w;
+                best_t = t;
+                for (int k = 0; k < 3; ++k) best_cap[k] = pass_cap[k];
+            }
         }
         if (rc) break;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    for (auto& e : ev) cudaEventDestroy(e);
+    // the O(N) kernels left their accumulators cleared; the last evaluation's
+    // force and chain accumulators are read out (and cleared) here
+    if (!rc) rc = gbk::launch_forces_out(atom_args(c, xyzq, rad), nullptr, nullptr, nullptr, s) == cudaSuccess
+                      ? GB_OK : GB_ERR_CUDA;
     if (rc) return rc;
-    c->tasks.min_blocks = best_m;
+    for (int k = 0; k < 3; ++k) c->tasks.cap[k] = best_cap[k];
     return gb_set_tiles(c, best_w, best_t);
 }
 

@@ -22,6 +22,7 @@ __device__ __forceinline__ double block_sum_d(double v, double* sh) {
 
 // --- Born radii: I -> psi -> R (OBC), see born_finalize_atom ----------------------
 __global__ void k_born_finalize(AtomArgs A, float* R_out) {
+    pdl_enter();
     const int r = blockIdx.y;
     const int64_t base = A.atom_off[r];
     const int n = (int)(A.atom_off[r + 1] - base);
@@ -32,6 +33,7 @@ __global__ void k_born_finalize(AtomArgs A, float* R_out) {
 
 // --- self terms, dE/dR -> chain factor, dE/dq readout ----------------------------
 __global__ void k_energy_finalize(AtomArgs A, int want_energy, double* phi_out) {
+    pdl_enter();
     __shared__ double sh[32];
     const int r = blockIdx.y;
     const int64_t base = A.atom_off[r];
@@ -57,6 +59,7 @@ __global__ void k_energy_finalize(AtomArgs A, int want_energy, double* phi_out) 
 
 // --- readout: int64 forces -> outputs; energies -> FP64; clear accumulators -------
 __global__ void k_forces_out(AtomArgs A, int64_t* F_fixed, float* F_out, double* E_out) {
+    pdl_enter();
     const int r = blockIdx.y;
     const int64_t base = A.atom_off[r];
     const int n = (int)(A.atom_off[r + 1] - base);
@@ -86,6 +89,7 @@ __global__ void k_forces_out(AtomArgs A, int64_t* F_fixed, float* F_out, double*
 // --- Langevin BAOAB ---------------------------------------------------------------
 // B (half kick), A (half drift), O (exact Ornstein-Uhlenbeck), A (half drift)
 __global__ void k_md_first(AtomArgs A, MDArgs m, int step_in_block) {
+    pdl_enter();
     const int r = blockIdx.y;
     const int64_t base = A.atom_off[r];
     const int n = (int)(A.atom_off[r + 1] - base);
@@ -102,6 +106,7 @@ __global__ void k_md_first(AtomArgs A, MDArgs m, int step_in_block) {
 // Total force (pair accumulators + chain bonds k (r - r0)^2) then the closing
 // half kick B; kick == 0 only stores the force (start of a trajectory).
 __global__ void k_md_second(AtomArgs A, MDArgs m, int kick) {
+    pdl_enter();
     const int r = blockIdx.y;
     const int64_t base = A.atom_off[r];
     const int n = (int)(A.atom_off[r + 1] - base);
@@ -127,11 +132,13 @@ __global__ void k_md_second(AtomArgs A, MDArgs m, int kick) {
 }
 
 __global__ void k_set_counters(u64* ctr, u64 step, u64 attempt) {
+    pdl_enter();
     ctr[0] = step;
     ctr[1] = attempt;
 }
 
 __global__ void k_advance_counters(u64* ctr, u64 steps, u64 attempts) {
+    pdl_enter();
     ctr[0] += steps;
     ctr[1] += attempts;
 }
@@ -196,6 +203,7 @@ __device__ __forceinline__ float mc_pair_term(float4 xk, float2 Rk, float4 xj, f
 }
 
 __global__ void __launch_bounds__(256) k_mc_rows(MCArgs A) {
+    pdl_enter();
     __shared__ MCPick s_pick;
     const int r = blockIdx.y, part = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
@@ -230,6 +238,7 @@ __global__ void __launch_bounds__(256) k_mc_rows(MCArgs A) {
 }
 
 __global__ void __launch_bounds__(256) k_mc_decide(MCArgs A) {
+    pdl_enter();
     __shared__ MCPick s_pick;
     __shared__ double s_phi[MC_MAX_SITE_ATOMS];
     __shared__ double s_dq[MC_MAX_SITE_ATOMS];
@@ -334,6 +343,7 @@ __device__ __forceinline__ int partner(int a, int len, u64 attempt, int wrap) {
 }
 
 __global__ void k_exchange(ExArgs A) {
+    pdl_enter();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= A.n_ladders * A.len) return;
     const int l = t / A.len, a = t % A.len;
@@ -358,6 +368,7 @@ __device__ __forceinline__ int bound_count(const GridExArgs& A, int rep, int kin
 }
 
 __global__ void k_grid_exchange(GridExArgs A) {
+    pdl_enter();
     const u64 attempt = A.ctr[1];
     const int dimE = (A.ex_dim == 0) || (A.ex_dim == 2 && ((attempt >> 1) & 1) == 0);
     const int n_lad = dimE ? A.n_pH : A.n_E;
@@ -387,6 +398,7 @@ __global__ void k_grid_exchange(GridExArgs A) {
 __global__ void k_count(const int32_t* site_off, const int32_t* site_kind, const int32_t* site_state_off,
                         const int32_t* n_H, const int32_t* n_e, const int32_t* state, int32_t kind,
                         int32_t M, int32_t* out) {
+    pdl_enter();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= M) return;
     int c = 0;
@@ -404,65 +416,57 @@ static dim3 atom_grid(const AtomArgs& a) {
 }
 
 cudaError_t launch_born_finalize(const AtomArgs& a, float* R_out, cudaStream_t s) {
-    k_born_finalize<<<atom_grid(a), 256, 0, s>>>(a, R_out);
-    return cudaGetLastError();
+    return launch_pdl(k_born_finalize, atom_grid(a), dim3(256), 0, s, a, R_out);
 }
 
 cudaError_t launch_energy_finalize(const AtomArgs& a, int want_energy, double* phi_out, cudaStream_t s) {
-    k_energy_finalize<<<atom_grid(a), 256, 0, s>>>(a, want_energy, phi_out);
-    return cudaGetLastError();
+    return launch_pdl(k_energy_finalize, atom_grid(a), dim3(256), 0, s, a, want_energy, phi_out);
 }
 
 cudaError_t launch_forces_out(const AtomArgs& a, int64_t* F_fixed, float* F_out, double* E_out,
                               cudaStream_t s) {
-    k_forces_out<<<atom_grid(a), 256, 0, s>>>(a, F_fixed, F_out, E_out);
-    return cudaGetLastError();
+    return launch_pdl(k_forces_out, atom_grid(a), dim3(256), 0, s, a, F_fixed, F_out, E_out);
 }
 
 cudaError_t launch_md_first(const AtomArgs& a, const MDArgs& m, int step_in_block, cudaStream_t s) {
-    k_md_first<<<atom_grid(a), 256, 0, s>>>(a, m, step_in_block);
-    return cudaGetLastError();
+    return launch_pdl(k_md_first, atom_grid(a), dim3(256), 0, s, a, m, step_in_block);
 }
 
 cudaError_t launch_md_second(const AtomArgs& a, const MDArgs& m, cudaStream_t s) {
-    k_md_second<<<atom_grid(a), 256, 0, s>>>(a, m, 1);
-    return cudaGetLastError();
+    return launch_pdl(k_md_second, atom_grid(a), dim3(256), 0, s, a, m, 1);
 }
 
 cudaError_t launch_md_force_only(const AtomArgs& a, const MDArgs& m, cudaStream_t s) {
-    k_md_second<<<atom_grid(a), 256, 0, s>>>(a, m, 0);
-    return cudaGetLastError();
+    return launch_pdl(k_md_second, atom_grid(a), dim3(256), 0, s, a, m, 0);
 }
 
 cudaError_t launch_set_counters(u64* ctr, u64 step, u64 attempt, cudaStream_t s) {
-    k_set_counters<<<1, 1, 0, s>>>(ctr, step, attempt);
-    return cudaGetLastError();
+    return launch_pdl(k_set_counters, dim3(1), dim3(1), 0, s, ctr, step, attempt);
 }
 
 cudaError_t launch_advance_counters(u64* ctr, u64 steps, u64 attempts, cudaStream_t s) {
-    k_advance_counters<<<1, 1, 0, s>>>(ctr, steps, attempts);
-    return cudaGetLastError();
+    return launch_pdl(k_advance_counters, dim3(1), dim3(1), 0, s, ctr, steps, attempts);
 }
 
 cudaError_t launch_mc(const MCArgs& a, int32_t M, cudaStream_t s) {
     if (M == 0) return cudaSuccess;
-    if (a.n_parts > 0) k_mc_rows<<<dim3((unsigned)a.n_parts, (unsigned)M), 256, 0, s>>>(a);
-    k_mc_decide<<<M, 256, 0, s>>>(a);
-    return cudaGetLastError();
+    if (a.n_parts > 0) {
+        const cudaError_t e = launch_pdl(k_mc_rows, dim3((unsigned)a.n_parts, (unsigned)M), dim3(256), 0, s, a);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_pdl(k_mc_decide, dim3(M), dim3(256), 0, s, a);
 }
 
 cudaError_t launch_exchange(const ExArgs& a, cudaStream_t s) {
     const int n = a.n_ladders * a.len;
     if (n == 0) return cudaSuccess;
-    k_exchange<<<(n + 255) / 256, 256, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(k_exchange, dim3((n + 255) / 256), dim3(256), 0, s, a);
 }
 
 cudaError_t launch_grid_exchange(const GridExArgs& a, cudaStream_t s) {
     const int n = a.n_pH * a.n_E;
     if (n < 2) return cudaSuccess;
-    k_grid_exchange<<<(n + 255) / 256, 256, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(k_grid_exchange, dim3((n + 255) / 256), dim3(256), 0, s, a);
 }
 
 cudaError_t launch_count(const int32_t* site_off, const int32_t* site_kind,
@@ -470,9 +474,8 @@ cudaError_t launch_count(const int32_t* site_off, const int32_t* site_kind,
                          const int32_t* state, int32_t kind, int32_t M, int32_t* out,
                          cudaStream_t s) {
     if (M == 0) return cudaSuccess;
-    k_count<<<(M + 127) / 128, 128, 0, s>>>(site_off, site_kind, site_state_off, n_H, n_e, state,
-                                            kind, M, out);
-    return cudaGetLastError();
+    return launch_pdl(k_count, dim3((M + 127) / 128), dim3(128), 0, s, site_off, site_kind, site_state_off, n_H,
+                      n_e, state, kind, M, out);
 }
 
 }  // namespace gbk

@@ -40,6 +40,36 @@ __device__ __forceinline__ float ghost_x(int local) { return 1.0e7f + 16.0f * (f
 
 __device__ __forceinline__ float shfl(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 
+// Programmatic dependent launch.  Kernels are launched with launch_pdl, so the
+// next kernel in the stream may be scheduled onto SMs while this one drains.
+// Every kernel therefore starts with pdl_wait() (returns once the previous
+// kernel in the stream has completed and its writes are visible; immediately
+// when there is none) before it touches memory, and then calls pdl_trigger()
+// to let its own successor be scheduled.  Results are those of plain stream
+// order; only launch latency and the block ramp are overlapped.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_enter() {
+    pdl_wait();
+    pdl_trigger();
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Philox4x64-10 (Salmon et al., SC'11): 10 rounds of two 64x64->128 multiplies
 // with the published multipliers, key bumped by the published Weyl constants.
 struct Philox4 {

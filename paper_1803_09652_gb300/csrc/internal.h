@@ -37,7 +37,9 @@ struct PairArgs {
 struct TaskList {
     int4* d_tasks = nullptr;
     int n_tasks = 0;
-    int min_blocks = 1;        // register cap of the pair kernels: 1 (compiler) or 3 per SM
+    // register cap of each pass's kernel (Born, energy, chain), as 256-thread
+    // blocks per SM: 1 (compiler's choice), 3 (80 registers) or 4 (64)
+    int cap[3] = {1, 1, 1};
 };
 
 enum PassKind { PASS_BORN = 0, PASS_ENERGY = 1, PASS_CHAIN = 2 };

@@ -70,6 +70,7 @@ int scratch_for_current_device(unsigned char** out) {
 // writes atom_off = {0, n}.
 __global__ void k_static_tasks(int n, int nb, int tpt, int n_tasks, int64_t total, int4* tasks,
                                int64_t* atom_off) {
+    gbk::pdl_enter();
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w == 0) {
         atom_off[0] = 0;
@@ -121,9 +122,9 @@ extern "C" int gb_energy_forces_static(int32_t n_atoms, const gb_params* params,
 
     // the accumulators keep the last call's contents: start from zero
     if (cudaMemsetAsync(base, 0, kAccEnd, s) != cudaSuccess) return GB_ERR_CUDA;
-    k_static_tasks<<<(n_tasks + 255) / 256, 256, 0, s>>>(n, nb, kTilesPerTask, n_tasks, total, tasks,
-                                                         atom_off);
-    if (cudaGetLastError() != cudaSuccess) return GB_ERR_CUDA;
+    if (gbk::launch_pdl(k_static_tasks, dim3((n_tasks + 255) / 256), dim3(256), 0, s, n, nb, kTilesPerTask, n_tasks,
+                        total, tasks, atom_off) != cudaSuccess)
+        return GB_ERR_CUDA;
 
     gbk::PairArgs pa{};
     pa.atom_off = atom_off;

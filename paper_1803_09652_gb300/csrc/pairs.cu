@@ -4,10 +4,11 @@
 
 namespace gbk {
 
-// MINB = 1 leaves the register count to the compiler; MINB = 3 caps it so that
-// three 256-thread blocks fit on an SM (more warps, a few spills).
+// MINB = 1 leaves the register count to the compiler; MINB = 3 or 4 caps it so
+// that three or four 256-thread blocks fit on an SM (more warps, some spills).
 template <class P, int FLAGS, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_pairs(PairArgs A, const int4* __restrict__ tasks, int n_tasks) {
+    pdl_enter();
     extern __shared__ long long s_acc[];
     const int lane = threadIdx.x & 31;
     const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -16,6 +17,7 @@ __global__ void __launch_bounds__(256, MINB) k_pairs(PairArgs A, const int4* __r
 }
 
 __global__ void k_tile_boxes(PairArgs A, int M, int total_tiles) {
+    pdl_enter();
     const int lane = threadIdx.x & 31;
     const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (t >= total_tiles) return;
@@ -24,33 +26,34 @@ __global__ void k_tile_boxes(PairArgs A, int M, int total_tiles) {
 
 cudaError_t launch_tile_boxes(const PairArgs& a, int M, int total_tiles, cudaStream_t s) {
     if (!a.boxes || total_tiles == 0) return cudaSuccess;
-    k_tile_boxes<<<(total_tiles + 7) / 8, 256, 0, s>>>(a, M, total_tiles);
-    return cudaGetLastError();
+    return launch_pdl(k_tile_boxes, dim3((total_tiles + 7) / 8), dim3(256), 0, s, a, M, total_tiles);
 }
 
 template <class P, int FLAGS>
-static cudaError_t go(const PairArgs& a, const TaskList& t, int wpb, cudaStream_t s) {
+static cudaError_t go(const PairArgs& a, const TaskList& t, int cap, int wpb, cudaStream_t s) {
     if (t.n_tasks == 0) return cudaSuccess;
     const int blocks = (t.n_tasks + wpb - 1) / wpb;
     const size_t smem = (size_t)wpb * P::NQ * 64 * sizeof(long long);
-    if (t.min_blocks >= 3) k_pairs<P, FLAGS, 3><<<blocks, 32 * wpb, smem, s>>>(a, t.d_tasks, t.n_tasks);
-    else k_pairs<P, FLAGS, 1><<<blocks, 32 * wpb, smem, s>>>(a, t.d_tasks, t.n_tasks);
-    return cudaGetLastError();
+    const dim3 g(blocks), b(32 * wpb);
+    if (cap >= 4) return launch_pdl(k_pairs<P, FLAGS, 4>, g, b, smem, s, a, t.d_tasks, t.n_tasks);
+    if (cap == 3) return launch_pdl(k_pairs<P, FLAGS, 3>, g, b, smem, s, a, t.d_tasks, t.n_tasks);
+    return launch_pdl(k_pairs<P, FLAGS, 1>, g, b, smem, s, a, t.d_tasks, t.n_tasks);
 }
 
 cudaError_t launch_pairs(int pass, int flags, const PairArgs& a, const TaskList& t, int wpb,
                          cudaStream_t s) {
-    if (pass == PASS_BORN) return go<Born, 0>(a, t, wpb, s);
-    if (pass == PASS_CHAIN) return go<Chain, 0>(a, t, wpb, s);
+    const int cap = t.cap[pass];
+    if (pass == PASS_BORN) return go<Born, 0>(a, t, cap, wpb, s);
+    if (pass == PASS_CHAIN) return go<Chain, 0>(a, t, cap, wpb, s);
     switch (flags & 7) {
-        case 0: return go<EnergyF<0>, 0>(a, t, wpb, s);
-        case 1: return go<EnergyF<1>, 1>(a, t, wpb, s);
-        case 2: return go<EnergyF<2>, 2>(a, t, wpb, s);
-        case 3: return go<EnergyF<3>, 3>(a, t, wpb, s);
-        case 4: return go<EnergyF<4>, 4>(a, t, wpb, s);
-        case 5: return go<EnergyF<5>, 5>(a, t, wpb, s);
-        case 6: return go<EnergyF<6>, 6>(a, t, wpb, s);
-        default: return go<EnergyF<7>, 7>(a, t, wpb, s);
+        case 0: return go<EnergyF<0>, 0>(a, t, cap, wpb, s);
+        case 1: return go<EnergyF<1>, 1>(a, t, cap, wpb, s);
+        case 2: return go<EnergyF<2>, 2>(a, t, cap, wpb, s);
+        case 3: return go<EnergyF<3>, 3>(a, t, cap, wpb, s);
+        case 4: return go<EnergyF<4>, 4>(a, t, cap, wpb, s);
+        case 5: return go<EnergyF<5>, 5>(a, t, cap, wpb, s);
+        case 6: return go<EnergyF<6>, 6>(a, t, cap, wpb, s);
+        default: return go<EnergyF<7>, 7>(a, t, cap, wpb, s);
     }
 }
 

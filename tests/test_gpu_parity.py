@@ -97,6 +97,34 @@ def test_repeat_and_tile_shapes_bitwise(pkg):
         assert np.array_equal(o["E"], ref["E"])
 
 
+def test_register_caps_and_autotune_bitwise(pkg):
+    """Register caps change only scheduling: results stay bitwise identical,
+    per pass and for the autotuner's choice."""
+    import torch
+    b = synth.random_batch([500, 260, 33], seed=7)
+    ref, _ = _run(pkg, b)
+    xyzq, rad = to_dev(b, device())
+    for caps in [(1, 1, 1), (4, 4, 4), (1, 3, 4), (4, 1, 3)]:
+        ctx = pkg.Context(b.atom_off)
+        for p, c in enumerate(caps):
+            ctx.set_reg_cap(c, p)
+        assert ctx.reg_caps() == caps
+        o = {k: v.cpu().numpy() for k, v in ctx.energy_forces(xyzq, rad).items()}
+        ctx.sync_status()
+        for k in ("F_fixed", "R", "E", "dEdq"):
+            assert np.array_equal(o[k], ref[k]), (caps, k)
+    ctx = pkg.Context(b.atom_off)
+    ctx.autotune(xyzq, rad)
+    assert all(c in (1, 3, 4) for c in ctx.reg_caps())
+    o = {k: v.cpu().numpy() for k, v in ctx.energy_forces(xyzq, rad).items()}
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    for k in ("F_fixed", "R", "E", "dEdq"):
+        assert np.array_equal(o[k], ref[k]), k
+    with pytest.raises(Exception):
+        ctx.set_reg_cap(2, 0)
+
+
 def test_charge_derivative_sums_to_twice_energy(pkg):
     b = synth.random_batch([400], seed=12)
     out, _ = _run(pkg, b)
