@@ -272,11 +272,14 @@ cudaError_t mark(gb_ctx* c, cudaEvent_t e, cudaStream_t s) {
     return c->capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
 }
 
+// md != null: an MD step; the chain-bond forces join the force accumulators
+// and the tile boxes were already built by k_md_step (build_boxes false).
 int evaluate(gb_ctx* c, const float* xyzq, const float* rad, float* R_out, int flags,
-             double* phi_out, cudaStream_t s, const cudaEvent_t* ev = nullptr) {
+             double* phi_out, cudaStream_t s, const cudaEvent_t* ev = nullptr,
+             const gbk::MDArgs* md = nullptr, bool build_boxes = true) {
     const gbk::PairArgs pa = pair_args(c, xyzq, rad);
     const gbk::AtomArgs aa = atom_args(c, xyzq, rad);
-    GB_CHECK(c, gbk::launch_tile_boxes(pa, c->M, c->n_tiles32, s));
+    if (build_boxes) GB_CHECK(c, gbk::launch_tile_boxes(pa, c->M, c->n_tiles32, s));
     if (ev) GB_CHECK(c, mark(c, ev[0], s));
     GB_CHECK(c, gbk::launch_pairs(gbk::PASS_BORN, 0, pa, c->tasks, c->wpb, s));
     if (ev) GB_CHECK(c, mark(c, ev[1], s));
@@ -284,7 +287,8 @@ int evaluate(gb_ctx* c, const float* xyzq, const float* rad, float* R_out, int f
     if (ev) GB_CHECK(c, mark(c, ev[2], s));
     GB_CHECK(c, gbk::launch_pairs(gbk::PASS_ENERGY, flags, pa, c->tasks, c->wpb, s));
     if (ev) GB_CHECK(c, mark(c, ev[3], s));
-    GB_CHECK(c, gbk::launch_energy_finalize(aa, (flags & gbk::EF_ENERGY) ? 1 : 0, phi_out, s));
+    GB_CHECK(c, gbk::launch_energy_finalize(aa, (flags & gbk::EF_ENERGY) ? 1 : 0, phi_out, s,
+                                            md ? md->bond_k : 0.0f, md ? md->bond_r0 : 0.0f));
     if (ev) GB_CHECK(c, mark(c, ev[4], s));
     GB_CHECK(c, gbk::launch_pairs(gbk::PASS_CHAIN, 0, pa, c->tasks, c->wpb, s));
     if (ev) GB_CHECK(c, mark(c, ev[5], s));
@@ -776,12 +780,15 @@ int enqueue_steps(gb_ctx* c, gb_md_state* st, const gb_sites* sites, int64_t len
         c->prof_steps = len;
         c->prof_steps_per_launch.clear();
     }
+    // B A O A of the first step; then per step the evaluation, the MC and
+    // exchange attempts due at its end (they read positions, radii and charges,
+    // none of which the closing half kick changes), and one launch that closes
+    // this step and opens the next.
+    GB_CHECK(c, gbk::launch_md_step(aa, m, c->boxes, c->tile_off, 0, gbk::MD_OPEN, s));
     for (int64_t k = 0; k < len; ++k) {
-        GB_CHECK(c, gbk::launch_md_first(aa, m, (int)k, s));
-        int rc = evaluate(c, xyzq, rad, st->R, flags, nullptr, s,
-                          c->prof ? &c->prof_ev[6 * k] : nullptr);
+        int rc = evaluate(c, xyzq, rad, st->R, flags, nullptr, s, c->prof ? &c->prof_ev[6 * k] : nullptr, &m,
+                          false);
         if (rc) return rc;
-        GB_CHECK(c, gbk::launch_md_second(aa, m, s));
         const int64_t t = (int64_t)st->step + k + 1;   // only its residues matter
         if (mc_due(t)) {
             rc = enqueue_mc(c, st, sites, k + 1, s);
@@ -791,6 +798,8 @@ int enqueue_steps(gb_ctx* c, gb_md_state* st, const gb_sites* sites, int64_t len
             rc = enqueue_exchange(c, st, sites, s);
             if (rc) return rc;
         }
+        const int mode = gbk::MD_CLOSE | gbk::MD_KICK | (k + 1 < len ? gbk::MD_OPEN : 0);
+        GB_CHECK(c, gbk::launch_md_step(aa, m, c->boxes, c->tile_off, (int)(k + 1), mode, s));
     }
     GB_CHECK(c, gbk::launch_advance_counters(c->ctr, (u64)len, 0, s));
     return GB_OK;
@@ -804,9 +813,10 @@ extern "C" int gb_md_init(gb_ctx* c, gb_md_state* st, void* stream) {
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     const int flags = (c->p.rep_k != 0.0f) ? gbk::EF_REP : 0;
-    rc = evaluate(c, st->xyzq, st->rad_screen, st->R, flags, nullptr, s);
+    const gbk::MDArgs m = md_args(c, st);
+    rc = evaluate(c, st->xyzq, st->rad_screen, st->R, flags, nullptr, s, nullptr, &m, true);
     if (rc) return rc;
-    GB_CHECK(c, gbk::launch_md_force_only(atom_args(c, st->xyzq, st->rad_screen), md_args(c, st), s));
+    GB_CHECK(c, gbk::launch_md_step(atom_args(c, st->xyzq, st->rad_screen), m, nullptr, nullptr, 0, gbk::MD_CLOSE, s));
     return GB_OK;
 }
 

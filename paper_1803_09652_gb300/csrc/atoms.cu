@@ -32,7 +32,9 @@ __global__ void k_born_finalize(AtomArgs A, float* R_out) {
 }
 
 // --- self terms, dE/dR -> chain factor, dE/dq readout ----------------------------
-__global__ void k_energy_finalize(AtomArgs A, int want_energy, double* phi_out) {
+// With bond_k != 0 (MD) the chain-bond forces k (r - r0)^2 join the force
+// accumulators here, while the positions are fixed between the passes.
+__global__ void k_energy_finalize(AtomArgs A, int want_energy, double* phi_out, float bond_k, float bond_r0) {
     pdl_enter();
     __shared__ double sh[32];
     const int r = blockIdx.y;
@@ -48,6 +50,12 @@ __global__ void k_energy_finalize(AtomArgs A, int want_energy, double* phi_out) 
         if (phi_out) {
             phi_out[g] = unfix(A.phi_acc[g]) - A.tau_ke * q / R;
             A.phi_acc[g] = 0;
+        }
+        if (bond_k != 0.0f) {
+            const float3 fb = bond_force_kr(bond_k, bond_r0, A.xyzq, base, i, n);
+            A.F_acc[g] = __ldcg(&A.F_acc[g]) + (u64)fix(fb.x);
+            A.F_acc[A.N + g] = __ldcg(&A.F_acc[A.N + g]) + (u64)fix(fb.y);
+            A.F_acc[2 * A.N + g] = __ldcg(&A.F_acc[2 * A.N + g]) + (u64)fix(fb.z);
         }
     }
     if (want_energy) {
@@ -87,47 +95,59 @@ __global__ void k_forces_out(AtomArgs A, int64_t* F_fixed, float* F_out, double*
 }
 
 // --- Langevin BAOAB ---------------------------------------------------------------
-// B (half kick), A (half drift), O (exact Ornstein-Uhlenbeck), A (half drift)
-__global__ void k_md_first(AtomArgs A, MDArgs m, int step_in_block) {
+// One launch between two force evaluations.  MD_CLOSE: the total force of the
+// evaluation just finished (pair accumulators, bonds included; cleared here)
+// becomes the stored force, and with MD_KICK the closing half kick B is
+// applied.  MD_OPEN: B A O A of the next step (step counter base + step_in_block
+// + 1) with the stored or just-closed force, then the bounding boxes of the
+// tiles at the new positions for the far-block test of the pair passes.
+__global__ void k_md_step(AtomArgs A, MDArgs m, float4* boxes, const int* tile_off, int step_in_block, int mode) {
     pdl_enter();
     const int r = blockIdx.y;
     const int64_t base = A.atom_off[r];
     const int n = (int)(A.atom_off[r + 1] - base);
+    if ((int)(blockIdx.x * blockDim.x) >= n) return;      // whole block past this replica
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int64_t g = base + i;
-    const u64 step = m.ctr[0] + (u64)step_in_block + 1;
-    float4 x = m.xyzq[g], v = m.vel[g];
-    baoab_first(m, x, v, m.force[g], md_normals(m.seed, (u64)r, step, (u64)i));
-    m.xyzq[g] = x;
-    m.vel[g] = v;
-}
-
-// Total force (pair accumulators + chain bonds k (r - r0)^2) then the closing
-// half kick B; kick == 0 only stores the force (start of a trajectory).
-__global__ void k_md_second(AtomArgs A, MDArgs m, int kick) {
-    pdl_enter();
-    const int r = blockIdx.y;
-    const int64_t base = A.atom_off[r];
-    const int n = (int)(A.atom_off[r + 1] - base);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int64_t g = base + i;
-    float fx = (float)unfix(A.F_acc[g]);
-    float fy = (float)unfix(A.F_acc[A.N + g]);
-    float fz = (float)unfix(A.F_acc[2 * A.N + g]);
-    A.F_acc[g] = 0;
-    A.F_acc[A.N + g] = 0;
-    A.F_acc[2 * A.N + g] = 0;
-    const float3 fb = bond_force(m, m.xyzq, base, i, n);
-    fx += fb.x; fy += fb.y; fz += fb.z;
-    m.force[g] = make_float4(fx, fy, fz, 0.0f);
-    if (kick) {
+    const bool valid = i < n;
+    float4 x = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (valid) {
+        const int64_t g = base + i;
         float4 v = m.vel[g];
-        v.x = fmaf(m.h * m.inv_m, fx, v.x);
-        v.y = fmaf(m.h * m.inv_m, fy, v.y);
-        v.z = fmaf(m.h * m.inv_m, fz, v.z);
+        float4 f;
+        if (mode & MD_CLOSE) {
+            f = make_float4((float)unfix(__ldcg(&A.F_acc[g])), (float)unfix(__ldcg(&A.F_acc[A.N + g])),
+                            (float)unfix(__ldcg(&A.F_acc[2 * A.N + g])), 0.0f);
+            A.F_acc[g] = 0;
+            A.F_acc[A.N + g] = 0;
+            A.F_acc[2 * A.N + g] = 0;
+            m.force[g] = f;
+            if (mode & MD_KICK) {
+                v.x = fmaf(m.h * m.inv_m, f.x, v.x);
+                v.y = fmaf(m.h * m.inv_m, f.y, v.y);
+                v.z = fmaf(m.h * m.inv_m, f.z, v.z);
+            }
+        } else {
+            f = m.force[g];
+        }
+        if (mode & MD_OPEN) {
+            const u64 step = m.ctr[0] + (u64)step_in_block + 1;
+            x = m.xyzq[g];
+            baoab_first(m, x, v, f, md_normals(m.seed, (u64)r, step, (u64)i));
+            m.xyzq[g] = x;
+        }
         m.vel[g] = v;
+    }
+    if ((mode & MD_OPEN) && boxes) {
+        const int t = i >> 5;                              // warp-uniform tile of the replica
+        if (32 * t < n) {
+            float a = 0.0f, sc = 0.0f;
+            if (valid) {
+                const float2 rs = A.rad[base + i];
+                a = rs.x - A.offset;
+                sc = rs.y * a;
+            }
+            tile_box_store(boxes, (int64_t)tile_off[r] + t, valid, x.x, x.y, x.z, a, sc);
+        }
     }
 }
 
@@ -419,8 +439,9 @@ cudaError_t launch_born_finalize(const AtomArgs& a, float* R_out, cudaStream_t s
     return launch_pdl(k_born_finalize, atom_grid(a), dim3(256), 0, s, a, R_out);
 }
 
-cudaError_t launch_energy_finalize(const AtomArgs& a, int want_energy, double* phi_out, cudaStream_t s) {
-    return launch_pdl(k_energy_finalize, atom_grid(a), dim3(256), 0, s, a, want_energy, phi_out);
+cudaError_t launch_energy_finalize(const AtomArgs& a, int want_energy, double* phi_out, cudaStream_t s,
+                                   float bond_k, float bond_r0) {
+    return launch_pdl(k_energy_finalize, atom_grid(a), dim3(256), 0, s, a, want_energy, phi_out, bond_k, bond_r0);
 }
 
 cudaError_t launch_forces_out(const AtomArgs& a, int64_t* F_fixed, float* F_out, double* E_out,
@@ -428,16 +449,9 @@ cudaError_t launch_forces_out(const AtomArgs& a, int64_t* F_fixed, float* F_out,
     return launch_pdl(k_forces_out, atom_grid(a), dim3(256), 0, s, a, F_fixed, F_out, E_out);
 }
 
-cudaError_t launch_md_first(const AtomArgs& a, const MDArgs& m, int step_in_block, cudaStream_t s) {
-    return launch_pdl(k_md_first, atom_grid(a), dim3(256), 0, s, a, m, step_in_block);
-}
-
-cudaError_t launch_md_second(const AtomArgs& a, const MDArgs& m, cudaStream_t s) {
-    return launch_pdl(k_md_second, atom_grid(a), dim3(256), 0, s, a, m, 1);
-}
-
-cudaError_t launch_md_force_only(const AtomArgs& a, const MDArgs& m, cudaStream_t s) {
-    return launch_pdl(k_md_second, atom_grid(a), dim3(256), 0, s, a, m, 0);
+cudaError_t launch_md_step(const AtomArgs& a, const MDArgs& m, float4* boxes, const int* tile_off,
+                           int step_in_block, int mode, cudaStream_t s) {
+    return launch_pdl(k_md_step, atom_grid(a), dim3(256), 0, s, a, m, boxes, tile_off, step_in_block, mode);
 }
 
 cudaError_t launch_set_counters(u64* ctr, u64 step, u64 attempt, cudaStream_t s) {

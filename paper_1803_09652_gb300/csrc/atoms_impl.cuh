@@ -82,9 +82,9 @@ __device__ __forceinline__ void baoab_first(const MDArgs& m, float4& x, float4& 
 
 // Harmonic chain bonds k (r - r0)^2 with atoms i-1 and i+1 of the replica:
 // force on atom i.
-__device__ __forceinline__ float3 bond_force(const MDArgs& m, const float4* xyzq, int64_t base, int i, int n) {
+__device__ __forceinline__ float3 bond_force_kr(float k, float r0, const float4* xyzq, int64_t base, int i, int n) {
     float3 f = make_float3(0.0f, 0.0f, 0.0f);
-    if (m.bond_k == 0.0f) return f;
+    if (k == 0.0f) return f;
     const float4 xi = __ldcg(&xyzq[base + i]);
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
@@ -94,10 +94,13 @@ __device__ __forceinline__ float3 bond_force(const MDArgs& m, const float4* xyzq
         const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
         const float rr = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
         // dE/dr = 2 k (r - r0); the force on i points along +d when stretched
-        const float s = 2.0f * m.bond_k * (rr - m.bond_r0) / rr;
-        f.x = fmaf(s, dx, f.x); f.y = fmaf(s, dy, f.y); f.z = fmaf(s, dz, f.z);
+        const float sc = 2.0f * k * (rr - r0) / rr;
+        f.x = fmaf(sc, dx, f.x); f.y = fmaf(sc, dy, f.y); f.z = fmaf(sc, dz, f.z);
     }
     return f;
+}
+__device__ __forceinline__ float3 bond_force(const MDArgs& m, const float4* xyzq, int64_t base, int i, int n) {
+    return bond_force_kr(m.bond_k, m.bond_r0, xyzq, base, i, n);
 }
 
 }  // namespace gbk

@@ -40,6 +40,32 @@ __device__ __forceinline__ float ghost_x(int local) { return 1.0e7f + 16.0f * (f
 
 __device__ __forceinline__ float shfl(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 
+// Bounding box of one 32-atom tile, reduced over the warp (every lane calls
+// it; lanes without an atom pass valid = false): lo.xyz with the largest
+// a = rho - offset, hi.xyz with the largest screened radius s, stored by
+// lane 0 at boxes[2t], boxes[2t + 1].
+__device__ __forceinline__ void tile_box_store(float4* boxes, int64_t t, bool valid, float x, float y, float z,
+                                               float a, float s) {
+    float x0 = valid ? x : INFINITY, y0 = valid ? y : INFINITY, z0 = valid ? z : INFINITY;
+    float x1 = valid ? x : -INFINITY, y1 = valid ? y : -INFINITY, z1 = valid ? z : -INFINITY;
+    float am = valid ? a : 0.0f, sm = valid ? s : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x0 = fminf(x0, __shfl_xor_sync(0xffffffffu, x0, o));
+        y0 = fminf(y0, __shfl_xor_sync(0xffffffffu, y0, o));
+        z0 = fminf(z0, __shfl_xor_sync(0xffffffffu, z0, o));
+        x1 = fmaxf(x1, __shfl_xor_sync(0xffffffffu, x1, o));
+        y1 = fmaxf(y1, __shfl_xor_sync(0xffffffffu, y1, o));
+        z1 = fmaxf(z1, __shfl_xor_sync(0xffffffffu, z1, o));
+        am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
+        sm = fmaxf(sm, __shfl_xor_sync(0xffffffffu, sm, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        boxes[2 * t] = make_float4(x0, y0, z0, am);
+        boxes[2 * t + 1] = make_float4(x1, y1, z1, sm);
+    }
+}
+
 // Programmatic dependent launch.  Kernels are launched with launch_pdl, so the
 // next kernel in the stream may be scheduled onto SMs while this one drains.
 // Every kernel therefore starts with pdl_wait() (returns once the previous

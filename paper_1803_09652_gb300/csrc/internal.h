@@ -78,8 +78,9 @@ struct AtomArgs {
 };
 
 cudaError_t launch_born_finalize(const AtomArgs& a, float* R_out, cudaStream_t s);
-cudaError_t launch_energy_finalize(const AtomArgs& a, int want_energy, double* phi_out,
-                                   cudaStream_t s);
+// bond_k != 0 adds the chain-bond forces (MD) to the force accumulators.
+cudaError_t launch_energy_finalize(const AtomArgs& a, int want_energy, double* phi_out, cudaStream_t s,
+                                   float bond_k = 0.0f, float bond_r0 = 0.0f);
 cudaError_t launch_forces_out(const AtomArgs& a, int64_t* F_fixed, float* F_out, double* E_out,
                               cudaStream_t s);
 
@@ -95,9 +96,12 @@ struct MDArgs {
     u64 seed;
 };
 
-cudaError_t launch_md_first(const AtomArgs& a, const MDArgs& m, int step_in_block, cudaStream_t s);
-cudaError_t launch_md_second(const AtomArgs& a, const MDArgs& m, cudaStream_t s);
-cudaError_t launch_md_force_only(const AtomArgs& a, const MDArgs& m, cudaStream_t s);
+// MD half steps between force evaluations (k_md_step): MD_CLOSE stores the
+// evaluated force (MD_KICK: and applies the closing half kick), MD_OPEN runs
+// B A O A of the next step and rebuilds the tile boxes (boxes may be null).
+enum { MD_CLOSE = 1, MD_KICK = 2, MD_OPEN = 4 };
+cudaError_t launch_md_step(const AtomArgs& a, const MDArgs& m, float4* boxes, const int* tile_off,
+                           int step_in_block, int mode, cudaStream_t s);
 cudaError_t launch_set_counters(u64* ctr, u64 step, u64 attempt, cudaStream_t s);
 cudaError_t launch_advance_counters(u64* ctr, u64 steps, u64 attempts, cudaStream_t s);
 

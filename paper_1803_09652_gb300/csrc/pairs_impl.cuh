@@ -662,30 +662,15 @@ __device__ __forceinline__ void tile_box_warp(const PairArgs& A, int M, int t, i
     const int64_t base = A.atom_off[r];
     const int n = (int)(A.atom_off[r + 1] - base);
     const int i = 32 * (t - A.tile_off[r]) + lane;
-    float x0 = INFINITY, y0 = INFINITY, z0 = INFINITY, x1 = -INFINITY, y1 = -INFINITY, z1 = -INFINITY;
-    float am = 0.0f, sm = 0.0f;
+    float x = 0.0f, y = 0.0f, z = 0.0f, am = 0.0f, sm = 0.0f;
     if (i < n) {
         const float4 p = __ldcg(&A.xyzq[base + i]);
         const float2 rs = A.rad[base + i];
-        x0 = x1 = p.x; y0 = y1 = p.y; z0 = z1 = p.z;
+        x = p.x; y = p.y; z = p.z;
         am = rs.x - A.offset;
         sm = rs.y * am;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        x0 = fminf(x0, __shfl_xor_sync(0xffffffffu, x0, o));
-        y0 = fminf(y0, __shfl_xor_sync(0xffffffffu, y0, o));
-        z0 = fminf(z0, __shfl_xor_sync(0xffffffffu, z0, o));
-        x1 = fmaxf(x1, __shfl_xor_sync(0xffffffffu, x1, o));
-        y1 = fmaxf(y1, __shfl_xor_sync(0xffffffffu, y1, o));
-        z1 = fmaxf(z1, __shfl_xor_sync(0xffffffffu, z1, o));
-        am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
-        sm = fmaxf(sm, __shfl_xor_sync(0xffffffffu, sm, o));
-    }
-    if (lane == 0) {
-        A.boxes[2 * t] = make_float4(x0, y0, z0, am);
-        A.boxes[2 * t + 1] = make_float4(x1, y1, z1, sm);
-    }
+    tile_box_store(A.boxes, t, i < n, x, y, z, am, sm);
 }
 
 
