@@ -160,6 +160,7 @@ __device__ __forceinline__ void load_xas(const PairArgs& A, int64_t base, int n,
 // --- pass 1: Born integrals I_i = sum_j H(r_ij; a_i, s_j) -----------------------
 struct Born {
     static constexpr int NQ = 1;      // int64 i-side accumulators per atom (shared memory)
+    static constexpr int UNROLL = 1;  // rotation steps unrolled (measured best per pass)
     struct IState {
         f2 nx, ny, nz, a, s, s2, hs3;   // nx = -x
     };
@@ -254,6 +255,7 @@ struct Born {
 // exp(-D) = 2^(r^2 (-h_i) h_j) is two multiplies and one ex2.
 struct Energy {
     static constexpr int NQ = 5;      // fx, fy, fz, dE/dR, dE/dq (shared memory)
+    static constexpr int UNROLL = 1;
     struct IState {
         f2 nx, ny, nz, q, R, nh;
         long long egb, ec, er;
@@ -416,6 +418,7 @@ struct Energy {
 //   -(dE/dr)/r = c_i * (-(dH(r; a_i, s_j)/dr)/r) + c_j * (-(dH(r; a_j, s_i)/dr)/r).
 struct Chain {
     static constexpr int NQ = 3;      // fx, fy, fz (shared memory)
+    static constexpr int UNROLL = 2;
     struct IState {
         f2 nx, ny, nz, a, s, s2, hs3, c;
     };
@@ -553,7 +556,7 @@ struct EnergyF : Energy {
 template <class P, int FLAGS, int MODE, bool FAR>
 __device__ __forceinline__ void run_tile(const PairArgs& A, const typename P::IState& is, typename P::JState& js,
                                          typename P::Part& ip, int i0, int jbase, int lane, int next) {
-#pragma unroll 2
+#pragma unroll P::UNROLL
     for (int k = 0; k < 32; ++k) {
         // the next step's j data are fetched before this step's arithmetic, so
         // that only the short accumulator chain is serial between steps
