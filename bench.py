@@ -36,8 +36,11 @@ MC_EVERY, EX_EVERY = 10, 100
 N_REP, N_ATOMS = 8, 2048
 SM_COUNT = 152
 FP32_LANES = 128           # FP32 lanes per SM
-# algorithmic FP32 flops per unordered pair (FMA = 2), per pass; see the design doc
-FLOPS_PER_PAIR = {"born": 57, "energy": 47, "chain": 80}
+# Algorithmic FP32 flops per unordered pair and pass (FMA = 2, add / mul = 1;
+# MUFU ops counted apart), counted on the far-field arithmetic every disjoint
+# pair needs (short polynomials); pairs in near blocks cost more, so these
+# figures are a lower bound of the FP32 work done (derivation in the design doc).
+FLOPS_PER_PAIR = {"born": 35.5, "energy": 46.0, "chain": 52.5}
 MUFU_PER_PAIR = {"born": 1, "energy": 3, "chain": 1}
 PASS_NAMES = ["born", "energy", "chain"]
 
@@ -96,42 +99,80 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------------
-def reference_arm(args):
-    """The FP64 oracle on host cores, on a bounded sample of the same workload:
-    each step = 2 MD steps of one 2048-atom replica (the 8 replicas are
-    identical and independent between exchanges)."""
+def _oracle_md_worker(job):
+    """One host process: the FP64 oracle's force evaluation + BAOAB step of one
+    2048-atom replica of the workload, repeated for `seconds` (at least
+    `min_steps` steps).  Returns (MD steps, seconds)."""
+    seconds, min_steps, seed = job
     import oracle
+    import synth
     oracle.build()
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return
     b = workload()
     one = b.replicas[0]
-    import synth
     sb = synth.Batch([one], pH=b.pH[:1], E=b.E[:1])
     x, q, rho, scr, off = oracle.batch_arrays(sb)
     v = np.zeros_like(x)
     p = oracle.default_params()
     F, _ = oracle.forces_all(off, x, q, rho, scr, p)
-    md_per = 2
-    for w in range(args.warmup):
-        for k in range(md_per):
-            oracle.md_step(off, x, v, q, rho, scr, F, 1, w * md_per + k + 1, p)
+    n = 0
     t0 = time.perf_counter()
-    for s in range(args.steps):
-        for k in range(md_per):
-            oracle.md_step(off, x, v, q, rho, scr, F, 1, 10_000 + s * md_per + k, p)
-    dt = time.perf_counter() - t0
-    pairs = one.n * (one.n - 1) // 2
-    value = pairs * md_per * args.steps / dt
+    while time.perf_counter() - t0 < seconds or n < min_steps:
+        oracle.md_step(off, x, v, q, rho, scr, F, seed, n + 1, p)
+        n += 1
+    return n, time.perf_counter() - t0
+
+
+def oracle_throughput(procs, seconds=0.0, min_steps=1):
+    """The oracle as it stands on `procs` host cores: one independent replica
+    per process (replicas are independent between exchanges), processes
+    started with spawn.  Returns (pair-interactions/s, MD steps, wall s)."""
+    import oracle
+    oracle.build()
+    pairs = N_ATOMS * (N_ATOMS - 1) // 2
+    jobs = [(seconds, min_steps, 1 + k) for k in range(procs)]
+    t0 = time.perf_counter()
+    if procs == 1:
+        res = [_oracle_md_worker(jobs[0])]
+    else:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(procs) as pool:
+            res = pool.map(_oracle_md_worker, jobs)
+    wall = time.perf_counter() - t0
+    steps = sum(r[0] for r in res)
+    # per-process rates summed: start-up of the spawned interpreters is not oracle work
+    rate = sum(pairs * r[0] / r[1] for r in res)
+    return rate, steps, wall
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def reference_arm(args):
+    """The FP64 oracle on all host cores, on a bounded sample of the same
+    workload: each step = 2 MD steps of one 2048-atom replica per core (the 8
+    replicas are identical and independent between exchanges)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    procs = host_cores()
+    md_per = 2
+    oracle_throughput(procs, 0.0, md_per * args.warmup) if args.warmup else None
+    rate, steps, wall = oracle_throughput(procs, 0.0, md_per * args.steps)
+    value = rate
     line = {
         "impl": "reference", "metric": "GB pair-interactions/s", "value": value,
         "unit": "pair-interactions/s", "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": 1000 * wall / max(args.steps, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"eremd_{N_REP}x{N_ATOMS}", "sample": "1 replica x 2 MD steps per step"},
-        "cpu_baseline": {"value": value, "unit": "pair-interactions/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} x 2 MD steps of one {one.n}-atom replica"},
+        "config": {"workload": f"eremd_{N_REP}x{N_ATOMS}",
+                   "sample": f"{procs} processes x {md_per} MD steps of one replica per step"},
+        "cpu_baseline": {"value": value, "unit": "pair-interactions/s", "cores": procs, "kind": "oracle",
+                         "sample": f"{steps} BAOAB MD steps of 2048-atom replicas, one per process, "
+                                   f"{procs} spawned processes"},
         "e2e": {"value": value, "unit": "pair-interactions/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -139,28 +180,16 @@ def reference_arm(args):
 
 
 def cpu_baseline(seconds=12.0):
-    """FP64 oracle force evaluation + BAOAB step of one 2048-atom replica,
-    repeated for about `seconds` of single-core CPU time."""
-    import oracle
-    import synth
-    oracle.build()
-    b = workload()
-    one = b.replicas[0]
-    sb = synth.Batch([one], pH=b.pH[:1], E=b.E[:1])
-    x, q, rho, scr, off = oracle.batch_arrays(sb)
-    v = np.zeros_like(x)
-    p = oracle.default_params()
-    F, _ = oracle.forces_all(off, x, q, rho, scr, p)
-    n_steps = 0
-    t0 = time.perf_counter()
-    while time.perf_counter() - t0 < seconds or n_steps < 3:
-        oracle.md_step(off, x, v, q, rho, scr, F, 1, n_steps + 1, p)
-        n_steps += 1
-    dt = time.perf_counter() - t0
-    pairs = one.n * (one.n - 1) // 2
-    return {"value": pairs * n_steps / dt, "unit": "pair-interactions/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n_steps} BAOAB MD steps (GB+Coulomb+restraint forces) of one {one.n}-atom replica, "
-                      f"{dt:.1f} s single-threaded"}
+    """The oracle's force evaluation + BAOAB step of 2048-atom replicas for
+    about `seconds`: on one core, then one replica per core on all cores."""
+    r1, n1, w1 = oracle_throughput(1, seconds, 3)
+    procs = host_cores()
+    rN, nN, wN = oracle_throughput(procs, seconds, 3)
+    return {"value": rN, "unit": "pair-interactions/s", "cores": procs, "kind": "oracle",
+            "sample": f"{nN} BAOAB MD steps (GB+Coulomb+restraint forces) of 2048-atom replicas, one per "
+                      f"process on {procs} cores, {seconds:.0f} s each",
+            "single_core": {"value": r1, "cores": 1,
+                            "sample": f"{n1} MD steps of one replica, {w1:.1f} s"}}
 
 
 # ----------------------------------------------------------------------------------
@@ -256,6 +285,35 @@ def launches_per_segment(md_steps, persistent=True):
     return 1 + md + mc + ex + 1                    # + set counters, + advance step counter
 
 
+# ---- one process per GPU: replicas only (each rank runs its own batch) --------
+def dist_init(backend):
+    """Rank layout from the launcher's environment; a process group only for
+    N > 1 (its barrier and max-over-ranks timing; no data-path collective)."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def max_over_ranks(seconds, world, device):
+    """The slowest rank's time: the whole job ends when it does."""
+    if world == 1:
+        return seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: every rank processed the same units (weak scaling)."""
+    return units_per_rank * world / seconds
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -273,12 +331,7 @@ def main():
         return
 
     import torch
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    world, rank, local = dist_init("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
@@ -326,13 +379,9 @@ def main():
     S.ctx.sync_status()
     step_ms = [a.elapsed_time(c) for a, c in ev]
     dev_s = sum(step_ms) / 1000.0
-    if world > 1:
-        t = torch.tensor([dev_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        dev_s = float(t.item())
-    total_pairs = pairs_md * MD_PER_STEP * args.steps * world
-    value = total_pairs / dev_s
-    rep_steps = b.n_rep * MD_PER_STEP * args.steps * world / dev_s
+    dev_s = max_over_ranks(dev_s, world, dev)
+    value = job_rate(pairs_md * MD_PER_STEP * args.steps, world, dev_s)
+    rep_steps = job_rate(b.n_rep * MD_PER_STEP * args.steps, world, dev_s)
 
     # ---- kernel timing: the same bench steps with CUDA events around every pair
     # pass (or persistent launch) inside the captured graph, on the graph's
@@ -365,7 +414,10 @@ def main():
         dom = int(np.argmax(pm))
         name = "k_pairs<%s>" % PASS_NAMES[dom]
         achieved = pairs_md * FLOPS_PER_PAIR[PASS_NAMES[dom]] / (pm[dom] * 1e-3) / 1e12
-        timing = {"pass_ms": dict(zip(PASS_NAMES, [float(v) for v in pm]))}
+        timing = {"pass_ms": dict(zip(PASS_NAMES, [float(v) for v in pm])),
+                  "pass_pairs_per_s": {k: pairs_md / (float(v) * 1e-3) for k, v in zip(PASS_NAMES, pm)},
+                  "pass_tflops": {k: pairs_md * FLOPS_PER_PAIR[k] / (float(v) * 1e-3) / 1e12
+                                  for k, v in zip(PASS_NAMES, pm)}}
     step_fp32 = all_flops * MD_PER_STEP * args.steps / dev_s / 1e12
     traffic = read_traffic(name)
 
@@ -397,6 +449,7 @@ def main():
             "replica_md_steps_per_s": rep_steps,
             "kernel_timing": timing,
             "fp32_flops_per_pair": FLOPS_PER_PAIR,
+            "mufu_per_pair": MUFU_PER_PAIR,
             "fp32_tflops_whole_step": step_fp32,
             "fp32_peak_frac_whole_step": step_fp32 / peak,
             "roofline": {"bound": "alu", "kernel": name, "achieved": achieved,
