@@ -26,9 +26,9 @@
  *      fixed forces int64[3][N]  components x, then y, then z; F * 2^32,
  *                                rounded (the accumulators themselves)
  *  - Arithmetic: FP32 pair terms; int64 fixed-point accumulation of forces,
- *    Born integrals, dE/dR and dE/dq; FP64 for the O(N) Born-radius
- *    transform, the per-replica energy totals, the Monte Carlo energy change
- *    and every acceptance test.
+ *    Born integrals, dE/dR and dE/dq; the O(N) Born-radius transform in FP32
+ *    written without cancellation; FP64 for the self terms, the per-replica
+ *    energy totals, the Monte Carlo energy change and every acceptance test.
  */
 #ifndef GBREMD_H
 #define GBREMD_H
