@@ -26,46 +26,6 @@
 
 namespace gbk {
 
-// --- HCT descreening integral H(r; a, s), closed form -----------------------------
-// H = (1/4pi) * volume integral of |y - x_i|^-4 over the part of the sphere
-// (centre x_j, radius s) that lies outside the sphere (x_i, a).  Closed form
-// from spherical shells about x_i between L = max(a, |r - s|) and U = r + s;
-// when x_i is engulfed (a < s - r) the full shells between a and s - r add
-// 1/a - 1/L.  It is used only where the spheres overlap (rare): there its
-// terms are O(1) and FP32 keeps them.
-static __device__ __noinline__ float hct_closed(float r, float rinv, float a, float s) {
-    if (a >= r + s) return 0.0f;
-    const float U = r + s;
-    const float L = fmaxf(a, fabsf(r - s));
-    const float iU = 1.0f / U, iL = 1.0f / L;
-    const float iU2 = iU * iU, iL2 = iL * iL;
-    float b = (iL - iU) + 0.25f * (r - s * s * rinv) * (iU2 - iL2) + 0.5f * rinv * logf(L * iU);
-    if (a < s - r) b += 2.0f * (1.0f / a - iL);
-    return 0.5f * b;
-}
-
-// -(dH/dr) / r of the closed form.
-static __device__ __noinline__ float hct_closed_fr(float r, float rinv, float a, float s) {
-    if (a >= r + s) return 0.0f;
-    const float U = r + s;
-    const float rs = r - s;
-    float L, dL;
-    if (a > fabsf(rs)) { L = a; dL = 0.0f; }
-    else { L = fabsf(rs); dL = rs > 0.0f ? 1.0f : -1.0f; }
-    const float iU = 1.0f / U, iL = 1.0f / L;
-    const float iU2 = iU * iU, iL2 = iL * iL;
-    const float w = r - s * s * rinv;           // r - s^2/r
-    const float dw = 1.0f + s * s * rinv * rinv; // d/dr of w
-    // b = 1/L - 1/U + (w/4)(1/U^2 - 1/L^2) + (1/(2r)) ln(L/U)
-    float db = -dL * iL2 + iU2
-             + 0.25f * dw * (iU2 - iL2)
-             + 0.5f * w * (dL * iL2 * iL - iU2 * iU)
-             - 0.5f * rinv * rinv * logf(L * iU)
-             + 0.5f * rinv * (dL * iL - iU);
-    if (a < s - r) db += 2.0f * dL * iL2;
-    return -0.5f * db * rinv;
-}
-
 // Disjoint spheres (r >= a + s) with x = s/r <= 0.6: H = 1/2 s^3 r^-4 g(x^2) and
 // -(dH/dr)/r = 1/2 s^3 r^-6 h(x^2), with g, h the fitted polynomials: no
 // cancellation and no MUFU.  Every lane evaluates the polynomial; the closed
@@ -106,6 +66,75 @@ __device__ __forceinline__ f2 ex22(f2 x) { return make_float2(ex2_ftz(x.x), ex2_
 constexpr float SQRT_LOG2E = 1.2011224087864498f;  // sqrt(log2(e))
 constexpr float LN2 = 0.69314718055994531f;
 constexpr float FAR_R2 = 1.0e30f;                  // r^2 given to masked-off lanes
+
+__device__ __forceinline__ f2 neg2(f2 v) { return make_float2(-v.x, -v.y); }
+// Reciprocal: MUFU estimate (flush-to-zero; arguments here are O(1) lengths)
+// and one Newton step y + y (1 - x y), which brings it to about half an ulp.
+__device__ __forceinline__ float rcp_ftz(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ f2 rcp2(f2 x) {
+    const f2 y = make_float2(rcp_ftz(x.x), rcp_ftz(x.y));
+    return fma2(y, fma2(neg2(x), y, F2(1.0f)), y);
+}
+__device__ __forceinline__ f2 logv(f2 x) { return make_float2(logf(x.x), logf(x.y)); }
+
+// --- HCT descreening integral H(r; a, s), closed form -----------------------------
+// H = (1/4pi) * volume integral of |y - x_i|^-4 over the part of the sphere
+// (centre x_j, radius s) that lies outside the sphere (x_i, a).  Closed form
+// from spherical shells about x_i between L = max(a, |r - s|) and U = r + s:
+//   H = 1/2 [1/L - 1/U + (r - s^2/r)/4 (1/U^2 - 1/L^2) + ln(L/U) / (2r)],
+// plus 1/a - 1/L inside the bracket when x_i is engulfed (a < s - r), and 0
+// when sphere j lies inside sphere i (a >= r + s).  It serves only pairs whose
+// spheres overlap or nearly touch (chain neighbours and contacts), where its
+// O(1) terms cancel to about a tenth of their size: the reciprocals and the
+// logarithm are kept to FP32 rounding.  Both pairs of a lane (x and y halves)
+// are evaluated at once, branch-free.
+__device__ __forceinline__ f2 hct_closed2(f2 r, f2 rinv, f2 a, f2 s) {
+    const f2 U = add2(r, s);
+    const f2 rs = add2(r, neg2(s));
+    const f2 L = make_float2(fmaxf(a.x, fabsf(rs.x)), fmaxf(a.y, fabsf(rs.y)));
+    const f2 iU = rcp2(U), iL = rcp2(L);
+    const f2 dU2 = add2(mul2(iU, iU), neg2(mul2(iL, iL)));        // 1/U^2 - 1/L^2
+    const f2 w = fma2(neg2(mul2(s, s)), rinv, r);                 // r - s^2/r
+    f2 b = fma2(mul2(F2(0.25f), w), dU2, add2(iL, neg2(iU)));
+    b = fma2(mul2(F2(0.5f), rinv), logv(mul2(L, iU)), b);        // ln(L/U) / (2r)
+    const f2 eng = mul2(F2(2.0f), add2(rcp2(a), neg2(iL)));       // engulfed: 2 (1/a - 1/L)
+    b.x += (a.x < -rs.x) ? eng.x : 0.0f;
+    b.y += (a.y < -rs.y) ? eng.y : 0.0f;
+    return make_float2(a.x >= U.x ? 0.0f : 0.5f * b.x, a.y >= U.y ? 0.0f : 0.5f * b.y);
+}
+
+// -(dH/dr) / r of the closed form, for both pairs of a lane.  With dL = dL/dr
+// (0 while L = a, sign(r - s) while L = |r - s|) and w = r - s^2/r:
+//   dB/dr = -dL/L^2 + 1/U^2 + (1 + s^2/r^2)/4 (1/U^2 - 1/L^2)
+//           + w/2 (dL/L^3 - 1/U^3) - ln(L/U) / (2 r^2) + (dL/L - 1/U) / (2r)
+// plus 2 dL/L^2 when engulfed; -(dH/dr)/r = -dB/dr / (2r).
+__device__ __forceinline__ f2 hct_closed_fr2(f2 r, f2 rinv, f2 a, f2 s) {
+    const f2 U = add2(r, s);
+    const f2 rs = add2(r, neg2(s));
+    const bool on_x = a.x > fabsf(rs.x), on_y = a.y > fabsf(rs.y);   // L = a
+    const f2 L = make_float2(on_x ? a.x : fabsf(rs.x), on_y ? a.y : fabsf(rs.y));
+    const f2 dL = make_float2(on_x ? 0.0f : (rs.x > 0.0f ? 1.0f : -1.0f),
+                              on_y ? 0.0f : (rs.y > 0.0f ? 1.0f : -1.0f));
+    const f2 iU = rcp2(U), iL = rcp2(L);
+    const f2 iU2 = mul2(iU, iU), iL2 = mul2(iL, iL);
+    const f2 s2r2 = mul2(mul2(s, s), mul2(rinv, rinv));           // s^2 / r^2
+    const f2 w = fma2(neg2(s2r2), r, r);                          // r - s^2/r
+    const f2 dLiL = mul2(dL, iL);
+    f2 db = fma2(neg2(dLiL), iL, iU2);                            // -dL/L^2 + 1/U^2
+    db = fma2(mul2(F2(0.25f), add2(F2(1.0f), s2r2)), add2(iU2, neg2(iL2)), db);
+    db = fma2(mul2(F2(0.5f), w), add2(mul2(dLiL, iL2), neg2(mul2(iU2, iU))), db);
+    const f2 hr = mul2(F2(0.5f), rinv);
+    db = fma2(neg2(mul2(hr, rinv)), logv(mul2(L, iU)), db);
+    db = fma2(hr, add2(dLiL, neg2(iU)), db);
+    db.x += (a.x < -rs.x) ? 2.0f * dLiL.x * iL.x : 0.0f;
+    db.y += (a.y < -rs.y) ? 2.0f * dLiL.y * iL.y : 0.0f;
+    const f2 fr = mul2(mul2(F2(-0.5f), db), rinv);
+    return make_float2(a.x >= U.x ? 0.0f : fr.x, a.y >= U.y ? 0.0f : fr.y);
+}
 
 __device__ __forceinline__ long long warp_sum_ll(long long v) {
 #pragma unroll
@@ -212,10 +241,14 @@ struct Born {
         const bool b0 = !far_ok(r.x, lim_ij.x, y_ij.x), b1 = !far_ok(r.y, lim_ij.y, y_ij.y);
         const bool c0 = !far_ok(r.x, lim_ji.x, y_ji.x), c1 = !far_ok(r.y, lim_ji.y, y_ji.y);
         if (__any_sync(0xffffffffu, b0 || b1 || c0 || c1)) {
-            if (b0) h_ij.x = hct_closed(r.x, rinv.x, i.a.x, j.s);
-            if (b1) h_ij.y = hct_closed(r.y, rinv.y, i.a.y, j.s);
-            if (c0) h_ji.x = hct_closed(r.x, rinv.x, j.a, i.s.x);
-            if (c1) h_ji.y = hct_closed(r.y, rinv.y, j.a, i.s.y);
+            if (__any_sync(0xffffffffu, b0 || b1)) {
+                const f2 hc = hct_closed2(r, rinv, i.a, F2(j.s));
+                h_ij = make_float2(b0 ? hc.x : h_ij.x, b1 ? hc.y : h_ij.y);
+            }
+            if (__any_sync(0xffffffffu, c0 || c1)) {
+                const f2 hc = hct_closed2(r, rinv, F2(j.a), i.s);
+                h_ji = make_float2(c0 ? hc.x : h_ji.x, c1 ? hc.y : h_ji.y);
+            }
         }
         h_ij = keep<MODE>(h_ij, m);
         h_ji = keep<MODE>(h_ji, m);
@@ -482,12 +515,17 @@ struct Chain {
         const bool b0 = !far_ok(r.x, lim_ij.x, y_ij.x), b1 = !far_ok(r.y, lim_ij.y, y_ij.y);
         const bool c0 = !far_ok(r.x, lim_ji.x, y_ji.x), c1 = !far_ok(r.y, lim_ji.y, y_ji.y);
         if (__any_sync(0xffffffffu, b0 || b1 || c0 || c1)) {
-            if (b0 || c0)
-                fr.x = (b0 ? i.c.x * hct_closed_fr(r.x, rinv.x, i.a.x, j.s) : t_ij.x * rinv6.x) +
-                       (c0 ? j.c * hct_closed_fr(r.x, rinv.x, j.a, i.s.x) : t_ji.x * rinv6.x);
-            if (b1 || c1)
-                fr.y = (b1 ? i.c.y * hct_closed_fr(r.y, rinv.y, i.a.y, j.s) : t_ij.y * rinv6.y) +
-                       (c1 ? j.c * hct_closed_fr(r.y, rinv.y, j.a, i.s.y) : t_ji.y * rinv6.y);
+            f2 fb = mul2(t_ij, rinv6), fc = mul2(t_ji, rinv6);
+            if (__any_sync(0xffffffffu, b0 || b1)) {
+                const f2 hc = mul2(i.c, hct_closed_fr2(r, rinv, i.a, F2(j.s)));
+                fb = make_float2(b0 ? hc.x : fb.x, b1 ? hc.y : fb.y);
+            }
+            if (__any_sync(0xffffffffu, c0 || c1)) {
+                const f2 hc = mul2(F2(j.c), hct_closed_fr2(r, rinv, F2(j.a), i.s));
+                fc = make_float2(c0 ? hc.x : fc.x, c1 ? hc.y : fc.y);
+            }
+            const f2 fbc = add2(fb, fc);
+            fr = make_float2(b0 || c0 ? fbc.x : fr.x, b1 || c1 ? fbc.y : fr.y);
         }
         fr = keep<MODE>(fr, m);
         p.sx = fma2(fr, dx, p.sx); p.sy = fma2(fr, dy, p.sy); p.sz = fma2(fr, dz, p.sz);
