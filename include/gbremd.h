@@ -235,7 +235,8 @@ typedef struct {
     const double* E_ladder; /* double[n_E] */
     const double* pH_ladder;/* double[n_pH] */
     int32_t n_E, n_pH;
-    double dt, friction, mass, kT;
+    double dt, friction, mass, kT;   /* ps, 1/ps, amu, kcal/mol; dt = 0 freezes the
+                                        coordinates (MC and exchange on a fixed structure) */
     float bond_k, bond_r0;
     uint64_t seed;
     uint64_t step;          /* absolute step counter, advanced by the call */

@@ -638,7 +638,7 @@ int check_md(gb_ctx* c, const gb_md_state* st) {
         return fail(c, GB_ERR_INVALID_ARG, "MD state buffer is NULL");
     if (!aligned(st->xyzq, 16) || !aligned(st->vel, 16) || !aligned(st->force, 16))
         return fail(c, GB_ERR_INVALID_ARG, "MD buffers must be 16-byte aligned");
-    if (!(st->dt > 0) || !(st->mass > 0) || !(st->kT > 0) || !(st->friction >= 0))
+    if (!(st->dt >= 0) || !(st->mass > 0) || !(st->kT > 0) || !(st->friction >= 0))
         return fail(c, GB_ERR_INVALID_ARG, "invalid MD constants");
     return GB_OK;
 }
