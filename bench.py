@@ -45,9 +45,22 @@ MUFU_PER_PAIR = {"born": 1, "energy": 3, "chain": 1}
 PASS_NAMES = ["born", "energy", "chain"]
 
 
-def workload():
+WORKLOADS = ("eremd_8x2048", "diff_16x4096", "uneven_64", "grid_48x25000")
+
+
+def workload(name="eremd_8x2048"):
+    """The batch of a named configuration (the headline is the E-REMD batch;
+    the others are the parity-test configurations, benched on request)."""
     import synth
-    return synth.config_eremd(N_REP, N_ATOMS, seed=0)
+    if name == "eremd_8x2048":
+        return synth.config_eremd(N_REP, N_ATOMS, seed=0)
+    if name == "diff_16x4096":
+        return synth.config_diff(16, 4096)
+    if name == "uneven_64":
+        return synth.config_uneven()
+    if name == "grid_48x25000":
+        return synth.config_grid()
+    raise ValueError(name)
 
 
 # ----------------------------------------------------------------------------------
@@ -212,21 +225,26 @@ class Setup:
         self.state = torch.zeros(self.tables["n_sites"], dtype=torch.int32, device=dev)
         self.pH = torch.as_tensor(batch.pH.copy(), device=dev)
         self.E = torch.as_tensor(batch.E.copy(), device=dev)
-        lad = batch.E_ladder if batch.E_ladder is not None else batch.E[:1]
-        self.E_ladder = torch.as_tensor(np.asarray(lad, np.float64), device=dev)
-        self.pH_ladder = torch.as_tensor(np.asarray([batch.pH[0]], np.float64), device=dev)
-        self.grid = torch.arange(M, dtype=torch.int32, device=dev)
+        E_lad = batch.E_ladder if batch.E_ladder is not None else batch.E[:1]
+        pH_lad = batch.pH_ladder if batch.pH_ladder is not None else batch.pH[:1]
+        self.E_ladder = torch.as_tensor(np.asarray(E_lad, np.float64), device=dev)
+        self.pH_ladder = torch.as_tensor(np.asarray(pH_lad, np.float64), device=dev)
+        self.grid = torch.arange(M, dtype=torch.int32, device=dev)   # replica p * n_E + e at (p, e)
+        # exchanges need a full ladder (or grid) of replicas; otherwise none
+        n_E, n_pH = len(E_lad), len(pH_lad)
+        ladder_ok = n_E * n_pH == M and M > 1
         st = pkg.MDState()
         st.xyzq, st.vel, st.force = self.xyzq.data_ptr(), self.vel.data_ptr(), self.force.data_ptr()
         st.rad_screen, st.R = self.rad.data_ptr(), self.R.data_ptr()
         st.state, st.pH, st.E = self.state.data_ptr(), self.pH.data_ptr(), self.E.data_ptr()
         st.grid, st.E_ladder, st.pH_ladder = (self.grid.data_ptr(), self.E_ladder.data_ptr(),
                                               self.pH_ladder.data_ptr())
-        st.n_E, st.n_pH = M, 1
+        st.n_E, st.n_pH = (n_E, n_pH) if ladder_ok else (M, 1)
         st.dt, st.friction, st.mass, st.kT = 0.002, 10.0, 12.0, pkg.KB * 300.0
         st.bond_k, st.bond_r0 = 300.0, 1.5
         st.seed, st.step, st.attempt = seed, 0, 0
-        st.mc_every, st.ex_every, st.ex_dim, st.wrap = MC_EVERY, EX_EVERY, 0, 1
+        st.mc_every, st.ex_every, st.wrap = MC_EVERY, EX_EVERY if ladder_ok else 0, 1
+        st.ex_dim = 2 if n_pH > 1 else 0          # alternate E and pH lines on a 2-D grid
         self.st = st
         self.ctx.md_init(st)
 
@@ -323,6 +341,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--workload", default="eremd_8x2048", choices=WORKLOADS,
+                    help="configuration to run (default: the E-REMD headline batch)")
     ap.add_argument("--persistent", action="store_true",
                     help="one persistent launch per run of MD steps instead of six launches per step")
     args = ap.parse_args()
@@ -344,7 +364,7 @@ def main():
     pkg.load()
 
     params = pkg.default_params(rep_k=10.0, rep_sigma=2.5)
-    b = workload()
+    b = workload(args.workload)
     S = Setup(pkg, b, dev, seed=1234 + rank, params=params)
     if not args.no_autotune:
         S.ctx.autotune(S.xyzq, S.rad)
@@ -424,7 +444,7 @@ def main():
     # ---- plain form: one context per replica, direct launches, no graph ---------
     plain = None
     if not args.no_plain and rank == 0:
-        plain = plain_form(pkg, b, dev, params, n_bench=max(1, min(3, args.steps)))
+        plain = plain_form(pkg, b, dev, params, n_bench=10)
 
     # ---- end to end through host buffers ----------------------------------------
     e2e = end_to_end(pkg, S, dev, n_bench=max(2, min(5, args.steps)), pairs_md=pairs_md)
@@ -440,8 +460,8 @@ def main():
             "ms_per_step": 1000 * dev_s / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 pairs, int64 fixed-point sums, f64 totals",
             "data": "synthetic",
-            "config": {"workload": f"eremd_{N_REP}x{N_ATOMS}", "replicas": b.n_rep,
-                       "atoms_per_replica": N_ATOMS, "md_steps_per_step": MD_PER_STEP,
+            "config": {"workload": args.workload, "replicas": b.n_rep,
+                       "atoms_total": b.n_atoms, "md_steps_per_step": MD_PER_STEP,
                        "mc_every": MC_EVERY, "exchange_every": EX_EVERY,
                        "pairs_per_md_step": pairs_md, "l2": "flushed between steps (256 MB write)",
                        "tiles": list(S.ctx.tiles()), "reg_caps": list(S.ctx.reg_caps()),
@@ -522,18 +542,19 @@ def plain_form(pkg, b, dev, params, n_bench):
     for S in setups:
         S.ctx.md_segment(S.st, S.sites, 10)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(n_bench):
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_bench)]
+    for k in range(n_bench):
+        ev[k][0].record()
         for t in range(MD_PER_STEP):
             for S in setups:
                 S.ctx.md_segment(S.st, S.sites, 1)
-    e1.record()
+        ev[k][1].record()
     torch.cuda.synchronize()
-    s = e0.elapsed_time(e1) / 1000.0
-    pairs = b.pairs_per_eval() * MD_PER_STEP * n_bench
-    return {"value": pairs / s, "unit": "pair-interactions/s", "ms_per_step": 1000 * s / n_bench,
-            "replica_md_steps_per_s": b.n_rep * MD_PER_STEP * n_bench / s,
+    ms = statistics.median(a.elapsed_time(c) for a, c in ev)      # per bench step
+    s = ms / 1000.0
+    pairs = b.pairs_per_eval() * MD_PER_STEP
+    return {"value": pairs / s, "unit": "pair-interactions/s", "ms_per_step": ms,
+            "replica_md_steps_per_s": b.n_rep * MD_PER_STEP / s, "bench_steps": n_bench, "statistic": "median",
             "form": "one context per replica, direct launches per MD step, no graph"}
 
 

@@ -196,3 +196,18 @@ def test_mc_decisions_eremd_8x2048(pkg):
             if near.any():
                 state.copy_(torch.as_tensor(st, device=dev))
                 xyzq[:, 3] = torch.as_tensor(q, dtype=torch.float32, device=dev)
+
+
+def test_single_replica_50000_atoms(pkg):
+    """Largest replica tested: one 50,000-atom chain (1.25e9 pairs, 782
+    tiles).  Sampled Born radii against the oracle one atom at a time, the
+    charge-derivative identity and the net force."""
+    rep = synth.make_replica(50000, 7, [(1, 20, 2), (0, 12, 2)])
+    b = synth.Batch([rep], pH=np.array([4.85]), E=np.array([synth.E0_REF_V]))
+    out = _gpu(pkg, b)
+    x, q, rho, scr, off = oracle.batch_arrays(b)
+    idx = np.random.default_rng(8).choice(50000, size=8, replace=False)
+    R = oracle.born_radii_subset(x, rho, scr, idx, oracle_params())
+    assert np.max(np.abs(out["R"][idx] - R) / R) <= R_REL
+    assert np.all(np.isfinite(out["F"])) and np.all(out["R"] > 0)
+    _properties(out, b)
