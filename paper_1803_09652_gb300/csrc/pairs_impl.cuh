@@ -149,6 +149,12 @@ __device__ __forceinline__ long long warp_sum_ll(long long v) {
 // tile is the x half's own tile and the y half is below the diagonal (off);
 // mode DY: the tile is the y half's own tile (x half fully on).
 enum { M_FULL = 0, M_DX = 1, M_DY = 2 };
+// Per-block bounds (see block_info): far block; r^2 >= t_near proves the
+// far-field form valid for both directions of a pair.
+struct BlockInfo {
+    bool far;
+    float t_near;
+};
 struct Mask {
     bool x, y;
 };
@@ -213,7 +219,7 @@ struct Born {
     }
     template <int FLAGS, int MODE, bool FAR>
     static __device__ __forceinline__ void pair(const PairArgs&, const IState& i, JState& j, Part& p, Mask m,
-                                                int, int, int) {
+                                                const BlockInfo& bi, int, int, int) {
         const f2 dx = add2(F2(j.x), i.nx), dy = add2(F2(j.y), i.ny), dz = add2(F2(j.z), i.nz);
         const f2 r2 = safe_r2<MODE>(fma2(dx, dx, fma2(dy, dy, mul2(dz, dz))), m);
         const f2 rinv = rsqrt2(r2);
@@ -226,6 +232,10 @@ struct Born {
             j.acc += h.x + h.y;
             return;
         }
+        // the block bound t_near decides most steps with one compare per lane;
+        // the exact per-direction tests run only on steps where some pair is
+        // closer
+        const float r2min = fminf(r2.x, r2.y);
         f2 g_ij, g_ji;
         if (all_far(y_ij, y_ji)) {
             g_ij = gb_poly_gf2(y_ij);
@@ -236,11 +246,11 @@ struct Born {
         }
         f2 h_ij = mul2(F2(0.5f * sj2 * j.s), mul2(rinv4, g_ij));
         f2 h_ji = mul2(i.hs3, mul2(rinv4, g_ji));
-        const f2 r = mul2(r2, rinv);
-        const f2 lim_ij = add2(i.a, F2(j.s)), lim_ji = add2(F2(j.a), i.s);
-        const bool b0 = !far_ok(r.x, lim_ij.x, y_ij.x), b1 = !far_ok(r.y, lim_ij.y, y_ij.y);
-        const bool c0 = !far_ok(r.x, lim_ji.x, y_ji.x), c1 = !far_ok(r.y, lim_ji.y, y_ji.y);
-        if (__any_sync(0xffffffffu, b0 || b1 || c0 || c1)) {
+        if (__any_sync(0xffffffffu, r2min < bi.t_near)) {
+            const f2 r = mul2(r2, rinv);
+            const f2 lim_ij = add2(i.a, F2(j.s)), lim_ji = add2(F2(j.a), i.s);
+            const bool b0 = !far_ok(r.x, lim_ij.x, y_ij.x), b1 = !far_ok(r.y, lim_ij.y, y_ij.y);
+            const bool c0 = !far_ok(r.x, lim_ji.x, y_ji.x), c1 = !far_ok(r.y, lim_ji.y, y_ji.y);
             if (__any_sync(0xffffffffu, b0 || b1)) {
                 const f2 hc = hct_closed2(r, rinv, i.a, F2(j.s));
                 h_ij = make_float2(b0 ? hc.x : h_ij.x, b1 ? hc.y : h_ij.y);
@@ -324,7 +334,7 @@ struct Energy {
     }
     template <int FLAGS, int MODE, bool FAR>
     static __device__ __forceinline__ void pair(const PairArgs& A, const IState& i, JState& j, Part& p, Mask m,
-                                                int i0, int jbase, int k) {
+                                                const BlockInfo&, int i0, int jbase, int k) {
         const f2 dx = add2(F2(j.x), i.nx), dy = add2(F2(j.y), i.ny), dz = add2(F2(j.z), i.nz);
         const f2 r2 = safe_r2<MODE>(fma2(dx, dx, fma2(dy, dy, mul2(dz, dz))), m);
         const f2 rinv = rsqrt2(r2);
@@ -480,7 +490,7 @@ struct Chain {
     }
     template <int FLAGS, int MODE, bool FAR>
     static __device__ __forceinline__ void pair(const PairArgs&, const IState& i, JState& j, Part& p, Mask m,
-                                                int, int, int) {
+                                                const BlockInfo& bi, int, int, int) {
         const f2 dx = add2(F2(j.x), i.nx), dy = add2(F2(j.y), i.ny), dz = add2(F2(j.z), i.nz);
         const f2 r2 = safe_r2<MODE>(fma2(dx, dx, fma2(dy, dy, mul2(dz, dz))), m);
         const f2 rinv = rsqrt2(r2);
@@ -498,6 +508,7 @@ struct Chain {
             return;
         }
         // c_i s_j^3/2 h(y_ij) + c_j s_i^3/2 h(y_ji), times r^-6
+        const float r2min = fminf(r2.x, r2.y);
         f2 p_ij, p_ji;
         if (all_far(y_ij, y_ji)) {
             p_ij = gb_poly_hf2(y_ij);
@@ -510,11 +521,11 @@ struct Chain {
         const f2 t_ji = mul2(mul2(F2(j.c), i.hs3), p_ji);
         const f2 rinv6 = mul2(rinv2, mul2(rinv2, rinv2));
         f2 fr = mul2(add2(t_ij, t_ji), rinv6);
-        const f2 r = mul2(r2, rinv);
-        const f2 lim_ij = add2(i.a, F2(j.s)), lim_ji = add2(F2(j.a), i.s);
-        const bool b0 = !far_ok(r.x, lim_ij.x, y_ij.x), b1 = !far_ok(r.y, lim_ij.y, y_ij.y);
-        const bool c0 = !far_ok(r.x, lim_ji.x, y_ji.x), c1 = !far_ok(r.y, lim_ji.y, y_ji.y);
-        if (__any_sync(0xffffffffu, b0 || b1 || c0 || c1)) {
+        if (__any_sync(0xffffffffu, r2min < bi.t_near)) {
+            const f2 r = mul2(r2, rinv);
+            const f2 lim_ij = add2(i.a, F2(j.s)), lim_ji = add2(F2(j.a), i.s);
+            const bool b0 = !far_ok(r.x, lim_ij.x, y_ij.x), b1 = !far_ok(r.y, lim_ij.y, y_ij.y);
+            const bool c0 = !far_ok(r.x, lim_ji.x, y_ji.x), c1 = !far_ok(r.y, lim_ji.y, y_ji.y);
             f2 fb = mul2(t_ij, rinv6), fc = mul2(t_ji, rinv6);
             if (__any_sync(0xffffffffu, b0 || b1)) {
                 const f2 hc = mul2(i.c, hct_closed_fr2(r, rinv, i.a, F2(j.s)));
@@ -593,7 +604,8 @@ struct EnergyF : Energy {
 // back in its home lane.
 template <class P, int FLAGS, int MODE, bool FAR>
 __device__ __forceinline__ void run_tile(const PairArgs& A, const typename P::IState& is, typename P::JState& js,
-                                         typename P::Part& ip, int i0, int jbase, int lane, int next) {
+                                         typename P::Part& ip, const BlockInfo& bi, int i0, int jbase, int lane,
+                                         int next) {
 #pragma unroll P::UNROLL
     for (int k = 0; k < 32; ++k) {
         // the next step's j data are fetched before this step's arithmetic, so
@@ -601,18 +613,27 @@ __device__ __forceinline__ void run_tile(const PairArgs& A, const typename P::IS
         typename P::JState nx = js;
         P::rotate_data(nx, next);
         const Mask m = step_mask<MODE>(k, lane);
-        P::template pair<FLAGS, MODE, FAR>(A, is, js, ip, m, i0, jbase, k);
+        P::template pair<FLAGS, MODE, FAR>(A, is, js, ip, m, bi, i0, jbase, k);
         P::rotate_acc(js, next);
         P::take_data(js, nx);
     }
 }
 
-// A block (super-row K, tile J) is "far" when the bounding boxes of its atoms
-// prove, for every pair, r >= a_i + s_j (disjoint spheres), (s/r)^2 <= YFAR
-// (short polynomial exact to FP32) and r >= the soft-repulsion range.  Boxes
-// (lo.xyz, max a) / (hi.xyz, max s) per 32-atom tile come from k_tile_boxes.
-__device__ __forceinline__ bool block_far(const PairArgs& A, int r, int K, int J, int nb) {
-    if (!A.boxes) return false;
+// Classification of a block (super-row K, tile J) from the bounding boxes of
+// its tiles (lo.xyz with max a, hi.xyz with max s, from k_tile_boxes).  The
+// block is "far" when the boxes prove, for every pair, r >= a_i + s_j
+// (disjoint spheres), (s/r)^2 <= YFAR (short polynomial exact to FP32) and
+// r >= the soft-repulsion range.  Otherwise r^2 >= t_near proves both
+// directions of a pair disjoint with (s/r)^2 <= YMAX (far-field form valid),
+// so only steps with a closer pair need the exact tests.  Without boxes
+// nothing is proven.
+__device__ __forceinline__ BlockInfo block_info(const PairArgs& A, int r, int K, int J, int nb) {
+    BlockInfo bi;
+    if (!A.boxes) {
+        bi.far = false;
+        bi.t_near = INFINITY;
+        return bi;
+    }
     const int t0 = A.tile_off[r];
     const float4 jl = __ldcg(&A.boxes[2 * (t0 + J)]), jh = __ldcg(&A.boxes[2 * (t0 + J) + 1]);
     float4 il = __ldcg(&A.boxes[2 * (t0 + 2 * K)]), ih = __ldcg(&A.boxes[2 * (t0 + 2 * K) + 1]);
@@ -627,9 +648,12 @@ __device__ __forceinline__ bool block_far(const PairArgs& A, int r, int K, int J
     const float rmin2 = gx * gx + gy * gy + gz * gz;
     const float amax = fmaxf(il.w, jl.w), smax = fmaxf(ih.w, jh.w);
     const float as = amax + smax;
-    bool far = rmin2 >= as * as && smax * smax <= GB_POLY_YFAR * rmin2;
-    if (A.rep_k != 0.0f) far = far && rmin2 >= A.rep_sigma * A.rep_sigma;
-    return far;
+    bi.far = rmin2 >= as * as && smax * smax <= GB_POLY_YFAR * rmin2;
+    if (A.rep_k != 0.0f) bi.far = bi.far && rmin2 >= A.rep_sigma * A.rep_sigma;
+    // thresholds rounded up a little, so that rounding in r^2 cannot admit a
+    // pair the exact test would reject
+    bi.t_near = 1.0001f * fmaxf(as * as, smax * smax * (1.0f / GB_POLY_YMAX));
+    return bi;
 }
 
 // Work of replica r is walked as super-rows K = 0 .. ceil(nb/2) - 1 (nb tiles
@@ -658,13 +682,14 @@ __device__ __forceinline__ void walk_task(const PairArgs& A, const int4 t, long 
         P::load_j(A, base, n, 32 * J + lane, js);
         typename P::Part ip;
         ip.zero();
+        const BlockInfo bi = block_info(A, r, K, J, nb);
         if (J >= 2 * K + 2) {
-            if (block_far(A, r, K, J, nb)) run_tile<P, FLAGS, M_FULL, true>(A, is, js, ip, 64 * K, 32 * J, lane, next);
-            else run_tile<P, FLAGS, M_FULL, false>(A, is, js, ip, 64 * K, 32 * J, lane, next);
+            if (bi.far) run_tile<P, FLAGS, M_FULL, true>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
+            else run_tile<P, FLAGS, M_FULL, false>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
         } else if (J == 2 * K) {
-            run_tile<P, FLAGS, M_DX, false>(A, is, js, ip, 64 * K, 32 * J, lane, next);
+            run_tile<P, FLAGS, M_DX, false>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
         } else {
-            run_tile<P, FLAGS, M_DY, false>(A, is, js, ip, 64 * K, 32 * J, lane, next);
+            run_tile<P, FLAGS, M_DY, false>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
         }
         P::fold_i(is, sa, lane, ip);
         P::flush_j(A, base, n, 32 * J + lane, js);
