@@ -70,6 +70,8 @@ def lib():
         _lib.gbo_restraints.argtypes = [i64, P, C.POINTER(Params), P, P]
         _lib.gbo_mc_step.argtypes = [i32, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P,
                                      P, P, d, u64, u64, i32, C.POINTER(Params), P, P, P, P, P, P]
+        _lib.gbo_mc_sweep.argtypes = [i32, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P,
+                                      P, P, d, u64, u64, i32, C.POINTER(Params), P, P, P, P, P]
         _lib.gbo_exchange.argtypes = [i32, i32, i32, i32, P, P, P, i32, u64, u64, d, i32, P, P]
         _lib.gbo_normals.argtypes = [u64, u64, u64, u64, P]
         _lib.gbo_forces_all.argtypes = [i32, P, P, P, P, P, C.POINTER(Params), P, P]
@@ -209,6 +211,29 @@ def mc_step(batch_off, x, q, R, tables, states, pH, E, kT, seed, step, kind,
         _p(np.ascontiguousarray(pH, np.float64)), _p(np.ascontiguousarray(E, np.float64)),
         float(kT), int(seed), int(step), int(kind), C.byref(p), _p(states), _p(out["dG"]),
         _p(out["acc"]), _p(out["thresh"]), _p(out["site"]), _p(out["new_state"]))
+    return out
+
+
+def mc_sweep(batch_off, x, q, R, tables, states, pH, E, kT, seed, step, kind,
+             p: Optional[Params] = None):
+    """Per-residue sweep (Sec. III.A.2): one attempt for every site of the
+    kind, in random order.  q and states are updated in place.  Returns dict of
+    per-site arrays: dG, acc (1 accepted, 0 rejected, 2 not of this kind),
+    thresh (= -kT ln u), visit (position in the replica's sweep, -1 if not)."""
+    p = p or default_params()
+    M = len(batch_off) - 1
+    S = int(tables["n_sites"])
+    out = dict(dG=np.zeros(S), acc=np.zeros(S, np.uint8), thresh=np.zeros(S),
+               visit=np.zeros(S, np.int32))
+    t = tables
+    lib().gbo_mc_sweep(
+        M, _p(np.ascontiguousarray(batch_off, np.int64)), _p(x), _p(q), _p(R),
+        _p(t["site_off"]), _p(t["site_kind"]), _p(t["site_nstates"]), _p(t["site_atom_off"]),
+        _p(t["site_atom_idx"]), _p(t["site_state_off"]), _p(t["site_q_off"]), _p(t["q_state"]),
+        _p(t["G_ref"]), _p(t["n_H"]), _p(t["n_e"]), _p(t["pKa_ref"]), _p(t["E0_ref"]),
+        _p(np.ascontiguousarray(pH, np.float64)), _p(np.ascontiguousarray(E, np.float64)),
+        float(kT), int(seed), int(step), int(kind), C.byref(p), _p(states), _p(out["dG"]),
+        _p(out["acc"]), _p(out["thresh"]), _p(out["visit"]))
     return out
 
 

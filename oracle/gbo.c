@@ -15,7 +15,8 @@
  *     descreening integral and the OBC rescaling of the integral into an
  *     effective Born radius, both restated below from their definitions.
  *   - Redox Monte Carlo criterion, Eq. 8 (Sec. II.A); protonation criterion,
- *     Eq. 9 (Sec. II.B); proposal and residue choice (Sec. III.A, III.A.1).
+ *     Eq. 9 (Sec. II.B); proposal and residue choice (Sec. III.A, III.A.1);
+ *     one attempt per residue in random order (Sec. III.A.2).
  *   - E-REMD exchange, Eq. 14-15 (Sec. II.C) and the neighbour schedule of
  *     Sec. III.B; pH exchange by analogy with Eq. 12 for protons.
  *   - Philox4x64-10 counter-based generator (Salmon, Moraes, Dror, Shaw,
@@ -409,6 +410,88 @@ void gbo_mc_step(int32_t n_rep, const int64_t* atom_off, const double* x, double
             state[site] = nxt;
         }
         free(q_new);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Per-residue sweep (Sec. III.A.2): one attempt for every site of the kind   */
+/* ------------------------------------------------------------------------ */
+
+/* Every site of the requested kind in replica r gets one state-change
+ * attempt, the sites taken in a uniformly random order (Sec. III.A.2); each
+ * attempt is the one of gbo_mc_step (new state uniform over the other states,
+ * dG of Eq. 8 / 9 from two energy evaluations at fixed R, Metropolis) with
+ * the charges left by the attempts before it.  Visit i (0-based) draws
+ * Philox(key (seed, 0), counter (r, step, 5 + kind, i)): word 0 picks the
+ * site among those not yet visited (a Fisher-Yates step over the sites of
+ * the kind in index order), word 1 the new state, word 2 gives u.  Per-site
+ * outputs (index = global site): dG, threshold -kT ln u, accepted flag,
+ * visit position; sites of the other kind get acc = 2 and visit = -1. */
+void gbo_mc_sweep(int32_t n_rep, const int64_t* atom_off, const double* x, double* q,
+                  const double* R, const int32_t* site_off, const int32_t* site_kind,
+                  const int32_t* site_nstates, const int32_t* site_atom_off,
+                  const int32_t* site_atom_idx, const int32_t* site_state_off,
+                  const int32_t* site_q_off, const float* q_state, const double* G_ref,
+                  const int32_t* n_H, const int32_t* n_e, const double* pKa_ref,
+                  const double* E0_ref, const double* pH, const double* Epot, double kT,
+                  uint64_t seed, uint64_t step, int32_t kind, const gbo_params* p,
+                  int32_t* state, double* dG_out, uint8_t* acc_out, double* thresh_out,
+                  int32_t* visit_out) {
+    for (int32_t r = 0; r < n_rep; ++r) {
+        for (int32_t s = site_off[r]; s < site_off[r + 1]; ++s) {
+            dG_out[s] = 0.0;
+            acc_out[s] = 2;
+            thresh_out[s] = 0.0;
+            visit_out[s] = -1;
+        }
+        int32_t n_kind = 0;
+        for (int32_t s = site_off[r]; s < site_off[r + 1]; ++s) n_kind += (site_kind[s] == kind);
+        if (n_kind == 0) continue;
+        int32_t* order = (int32_t*)malloc(sizeof(int32_t) * (size_t)n_kind);
+        for (int32_t s = site_off[r], c = 0; s < site_off[r + 1]; ++s)
+            if (site_kind[s] == kind) order[c++] = s;
+        int64_t n = atom_off[r + 1] - atom_off[r];
+        const double* xr = x + 3 * atom_off[r];
+        double* qr = q + atom_off[r];
+        const double* Rr = R + atom_off[r];
+        double* q_new = (double*)malloc(sizeof(double) * (size_t)n);
+        for (int32_t i = 0; i < n_kind; ++i) {
+            uint64_t w[4];
+            draw(seed, (uint64_t)r, step, 5 + (uint64_t)kind, (uint64_t)i, w);
+            int32_t j = i + pick(w[0], n_kind - i);
+            int32_t tmp = order[i];
+            order[i] = order[j];
+            order[j] = tmp;
+            int32_t site = order[i];
+            int32_t cur = state[site];
+            int32_t k = pick(w[1], site_nstates[site] - 1);
+            int32_t nxt = (k < cur) ? k : k + 1;
+            int32_t na = site_atom_off[site + 1] - site_atom_off[site];
+            memcpy(q_new, qr, sizeof(double) * (size_t)n);
+            for (int32_t a = 0; a < na; ++a)
+                q_new[site_atom_idx[site_atom_off[site] + a]] =
+                    (double)q_state[site_q_off[site] + nxt * na + a];
+            double E0[2], E1[2];
+            gbo_energy_fixed_radii(n, xr, qr, Rr, p, E0);
+            gbo_energy_fixed_radii(n, xr, q_new, Rr, p, E1);
+            double dE = (E1[0] + E1[1]) - (E0[0] + E0[1]);
+            int32_t so = site_state_off[site];
+            double dG = dE - (G_ref[so + nxt] - G_ref[so + cur]);
+            dG += GBO_FARADAY * (Epot[r] - E0_ref[site]) * (double)(n_e[so + nxt] - n_e[so + cur]);
+            dG += kT * GBO_LN10 * (pH[r] - pKa_ref[site]) * (double)(n_H[so + nxt] - n_H[so + cur]);
+            double u = unif53(w[2]);
+            int acc = (dG <= 0.0) || (u < exp(-dG / kT));
+            dG_out[site] = dG;
+            acc_out[site] = (uint8_t)acc;
+            thresh_out[site] = (u > 0.0) ? -kT * log(u) : INFINITY;
+            visit_out[site] = i;
+            if (acc) {
+                memcpy(qr, q_new, sizeof(double) * (size_t)n);
+                state[site] = nxt;
+            }
+        }
+        free(q_new);
+        free(order);
     }
 }
 
