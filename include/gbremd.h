@@ -187,6 +187,29 @@ int redox_ph_mc_step(gb_ctx* ctx, const gb_sites* sites, float* xyzq, const floa
                      int32_t kind, int32_t* state_inout, double* dG_out, uint8_t* acc_out,
                      void* stream);
 
+/* Per-residue sweep: every site of the requested kind in every replica gets
+ * one state-change attempt, the sites of a replica taken in a uniformly
+ * random order -- the visiting rule of the explicit-solvent scheme (Sec.
+ * III.A.2), here with the same GB energies as redox_ph_mc_step (no solvent
+ * stripping or relaxation).  Each attempt is the one of redox_ph_mc_step
+ * (uniform new state, dG of Eq. 8 / 9 at fixed R, Metropolis) with the
+ * charges left by the attempts before it.  Random numbers: Philox4x64-10, key
+ * (seed, 0), counter (replica, step, 5 + kind, i) for visit i: word 0 picks
+ * the next site among those not yet visited (a Fisher-Yates step over the
+ * replica's sites of the kind in index order), word 1 the state, word 2 u.
+ *   arguments as in redox_ph_mc_step, except the outputs, which are per SITE:
+ *   dG_out     double[S] (nullable): dG of the site's attempt, 0 if not visited
+ *   acc_out    uint8[S]  (nullable): 1 accepted, 0 rejected, 2 not of this kind
+ * Limits per replica and kind: 256 sites, 1024 site atoms, 128 atoms per site;
+ * a replica over them is skipped and GB_ERR_INVALID_ARG is recorded for
+ * gb_sync_status.  The first call on a context allocates its workspace
+ * (8 bytes x replicas x ceil(largest replica / 256) x 1024); make it outside
+ * stream capture. */
+int redox_ph_mc_sweep(gb_ctx* ctx, const gb_sites* sites, float* xyzq, const float* R,
+                      const double* pH, const double* E, double kT, uint64_t seed, uint64_t step,
+                      int32_t kind, int32_t* state_inout, double* dG_out, uint8_t* acc_out,
+                      void* stream);
+
 /* Replica exchange between neighbouring slots of one or more ladders
  * (E-REMD, Eq. 14-15 and Sec. III.B; pH ladders by the same argument with
  * protons, Eq. 12 analogue).  Ladder l, slot k is occupied by replica
@@ -242,6 +265,8 @@ typedef struct {
     uint64_t step;          /* absolute step counter, advanced by the call */
     uint64_t attempt;       /* exchange attempt counter, advanced by the call */
     int32_t mc_every, ex_every, ex_dim, wrap;
+    int32_t mc_mode;        /* 0: one residue per attempt (redox_ph_mc_step, the implicit-
+                               solvent scheme); 1: every residue once (redox_ph_mc_sweep) */
 } gb_md_state;
 
 /* Advance the batch by nsteps MD steps.  Step t (1-based, absolute) is

@@ -74,7 +74,7 @@ class MDState(C.Structure):
                 ("kT", C.c_double), ("bond_k", C.c_float), ("bond_r0", C.c_float),
                 ("seed", C.c_uint64), ("step", C.c_uint64), ("attempt", C.c_uint64),
                 ("mc_every", C.c_int32), ("ex_every", C.c_int32), ("ex_dim", C.c_int32),
-                ("wrap", C.c_int32)]
+                ("wrap", C.c_int32), ("mc_mode", C.c_int32)]
 
 
 _lib = None
@@ -109,6 +109,7 @@ def load(path: Optional[str] = None):
         "gb_born_radii": [_P, _P, _P, _P, _P],
         "gb_energy_forces": [_P, _P, _P, _P, _P, _P, _P, _P, _P],
         "redox_ph_mc_step": [_P, C.POINTER(Sites), _P, _P, _P, _P, d, u64, u64, i32, _P, _P, _P, _P],
+        "redox_ph_mc_sweep": [_P, C.POINTER(Sites), _P, _P, _P, _P, d, u64, u64, i32, _P, _P, _P, _P],
         "eremd_exchange": [i32, i32, i32, i32, _P, _P, _P, i32, u64, u64, d, i32, _P, _P, _P, _P],
         "gb_count_bound": [C.POINTER(Sites), _P, i32, _P, _P],
         "gb_md_init": [_P, C.POINTER(MDState), _P],
@@ -282,6 +283,23 @@ class Context:
                                        _ptr(state), _ptr(dG_out), _ptr(acc_out), _stream(stream))
         _check(rc, self.h)
         return dG_out, acc_out
+
+    def mc_sweep(self, sites: SiteTables, xyzq, R, pH, E, kT, seed, step, kind, state,
+                 dG_out=None, acc_out=None, stream=None):
+        """Per-residue sweep: one attempt for every site of the kind (per-site
+        outputs; acc 2 marks sites of the other kind)."""
+        import torch
+        dev = xyzq.device
+        S = sites.struct.n_sites
+        if dG_out is None:
+            dG_out = torch.empty(max(S, 1), dtype=torch.float64, device=dev)
+        if acc_out is None:
+            acc_out = torch.empty(max(S, 1), dtype=torch.uint8, device=dev)
+        rc = self.lib.redox_ph_mc_sweep(self.h, C.byref(sites.struct), _ptr(xyzq), _ptr(R), _ptr(pH),
+                                        _ptr(E), float(kT), int(seed), int(step), int(kind),
+                                        _ptr(state), _ptr(dG_out), _ptr(acc_out), _stream(stream))
+        _check(rc, self.h)
+        return dG_out[:S], acc_out[:S]
 
     # -- MD ---------------------------------------------------------------------------
     def md_init(self, st: MDState, stream=None):

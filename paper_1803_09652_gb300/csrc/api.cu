@@ -30,6 +30,7 @@ struct gb_ctx {
     float* cc = nullptr;
     int* err = nullptr;
     double* mc_part = nullptr;          // MC site-row slice partials
+    double* sweep_part = nullptr;       // the same for per-residue sweeps (allocated on first use)
     float4* boxes = nullptr;            // tile bounding boxes
     int* tile_off = nullptr;
     int n_tiles32 = 0;
@@ -420,6 +421,7 @@ extern "C" int gb_ctx_destroy(gb_ctx* c) {
     cudaFree(c->cc);
     cudaFree(c->err);
     cudaFree(c->mc_part);
+    cudaFree(c->sweep_part);
     cudaFree(c->boxes);
     cudaFree(c->tile_off);
     if (c->cs) cudaStreamDestroy(c->cs);
@@ -523,18 +525,9 @@ extern "C" int gb_energy_forces(gb_ctx* c, const float* xyzq, const float* rad, 
     return GB_OK;
 }
 
-extern "C" int redox_ph_mc_step(gb_ctx* c, const gb_sites* sites, float* xyzq, const float* R,
-                                const double* pH, const double* E, double kT, uint64_t seed,
-                                uint64_t step, int32_t kind, int32_t* state, double* dG_out,
-                                uint8_t* acc_out, void* stream) {
-    if (!c) return fail(nullptr, GB_ERR_INVALID_ARG, "NULL context");
-    int rc = check_sites(c, sites);
-    if (rc) return rc;
-    if (!xyzq || !R || !pH || !E || !state) return fail(c, GB_ERR_INVALID_ARG, "NULL array");
-    if (kind != 0 && kind != 1) return fail(c, GB_ERR_INVALID_ARG, "kind must be 0 (pH) or 1 (redox)");
-    if (!(kT > 0.0)) return fail(c, GB_ERR_INVALID_ARG, "kT must be positive");
-    if (!aligned(xyzq, 16)) return fail(c, GB_ERR_INVALID_ARG, "xyzq must be 16-byte aligned");
-    DeviceGuard g(c->device);
+static gbk::MCArgs mc_args(const gb_ctx* c, const gb_sites* sites, float* xyzq, const float* R,
+                           const double* pH, const double* E, double kT, uint64_t seed, uint64_t step,
+                           int32_t kind, int32_t* state, double* dG_out, uint8_t* acc_out) {
     gbk::MCArgs a{};
     a.atom_off = c->off_d;
     a.site_off = sites->site_off;
@@ -564,9 +557,60 @@ extern "C" int redox_ph_mc_step(gb_ctx* c, const gb_sites* sites, float* xyzq, c
     a.state = state;
     a.dG_out = dG_out;
     a.acc_out = acc_out;
-    a.phi_part = c->mc_part;
     a.n_parts = c->mc_parts;
+    a.err = c->err;
+    return a;
+}
+
+// Workspace of per-residue sweeps, allocated on first use (outside capture).
+static int ensure_sweep_part(gb_ctx* c) {
+    if (c->sweep_part) return GB_OK;
+    const size_t n = (size_t)c->M * std::max(c->mc_parts, 1) * gbk::SWEEP_MAX_SITE_ATOMS;
+    cudaError_t e = cudaMalloc((void**)&c->sweep_part, n * sizeof(double));
+    if (e != cudaSuccess) {
+        c->sweep_part = nullptr;
+        return cuda_fail(c, e, "sweep workspace");
+    }
+    return GB_OK;
+}
+
+static int check_mc(gb_ctx* c, const gb_sites* sites, float* xyzq, const float* R, const double* pH,
+                    const double* E, double kT, int32_t kind, int32_t* state) {
+    if (!c) return fail(nullptr, GB_ERR_INVALID_ARG, "NULL context");
+    int rc = check_sites(c, sites);
+    if (rc) return rc;
+    if (!xyzq || !R || !pH || !E || !state) return fail(c, GB_ERR_INVALID_ARG, "NULL array");
+    if (kind != 0 && kind != 1) return fail(c, GB_ERR_INVALID_ARG, "kind must be 0 (pH) or 1 (redox)");
+    if (!(kT > 0.0)) return fail(c, GB_ERR_INVALID_ARG, "kT must be positive");
+    if (!aligned(xyzq, 16)) return fail(c, GB_ERR_INVALID_ARG, "xyzq must be 16-byte aligned");
+    return GB_OK;
+}
+
+extern "C" int redox_ph_mc_step(gb_ctx* c, const gb_sites* sites, float* xyzq, const float* R,
+                                const double* pH, const double* E, double kT, uint64_t seed,
+                                uint64_t step, int32_t kind, int32_t* state, double* dG_out,
+                                uint8_t* acc_out, void* stream) {
+    int rc = check_mc(c, sites, xyzq, R, pH, E, kT, kind, state);
+    if (rc) return rc;
+    DeviceGuard g(c->device);
+    gbk::MCArgs a = mc_args(c, sites, xyzq, R, pH, E, kT, seed, step, kind, state, dG_out, acc_out);
+    a.phi_part = c->mc_part;
     GB_CHECK(c, gbk::launch_mc(a, c->M, (cudaStream_t)stream));
+    return GB_OK;
+}
+
+extern "C" int redox_ph_mc_sweep(gb_ctx* c, const gb_sites* sites, float* xyzq, const float* R,
+                                 const double* pH, const double* E, double kT, uint64_t seed,
+                                 uint64_t step, int32_t kind, int32_t* state, double* dG_out,
+                                 uint8_t* acc_out, void* stream) {
+    int rc = check_mc(c, sites, xyzq, R, pH, E, kT, kind, state);
+    if (rc) return rc;
+    DeviceGuard g(c->device);
+    rc = ensure_sweep_part(c);
+    if (rc) return rc;
+    gbk::MCArgs a = mc_args(c, sites, xyzq, R, pH, E, kT, seed, step, kind, state, dG_out, acc_out);
+    a.phi_part = c->sweep_part;
+    GB_CHECK(c, gbk::launch_mc_sweep(a, c->M, (cudaStream_t)stream));
     return GB_OK;
 }
 
@@ -640,6 +684,7 @@ int check_md(gb_ctx* c, const gb_md_state* st) {
         return fail(c, GB_ERR_INVALID_ARG, "MD buffers must be 16-byte aligned");
     if (!(st->dt >= 0) || !(st->mass > 0) || !(st->kT > 0) || !(st->friction >= 0))
         return fail(c, GB_ERR_INVALID_ARG, "invalid MD constants");
+    if (st->mc_mode != 0 && st->mc_mode != 1) return fail(c, GB_ERR_INVALID_ARG, "mc_mode must be 0 or 1");
     return GB_OK;
 }
 
@@ -677,12 +722,19 @@ int enqueue_mc(gb_ctx* c, gb_md_state* st, const gb_sites* sites, int64_t k, cud
         a.state = st->state;
         a.dG_out = nullptr;
         a.acc_out = nullptr;
-        a.phi_part = c->mc_part;
         a.n_parts = c->mc_parts;
-        GB_CHECK(c, gbk::launch_mc(a, c->M, s));
+        a.err = c->err;
+        if (st->mc_mode == 1) {
+            a.phi_part = c->sweep_part;
+            GB_CHECK(c, gbk::launch_mc_sweep(a, c->M, s));
+        } else {
+            a.phi_part = c->mc_part;
+            GB_CHECK(c, gbk::launch_mc(a, c->M, s));
+        }
     }
     return GB_OK;
 }
+
 
 // Neighbour exchange on the (pH x E) grid; the attempt number is ctr[1], which
 // the second kernel advances.
@@ -835,6 +887,10 @@ extern "C" int gb_md_segment(gb_ctx* c, gb_md_state* st, const gb_sites* sites, 
     }
     if (nsteps == 0) return GB_OK;
     DeviceGuard g(c->device);
+    if (sites && st->mc_every > 0 && st->mc_mode == 1) {
+        rc = ensure_sweep_part(c);
+        if (rc) return rc;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     // one captured block covers a whole number of MC and exchange periods
     int64_t L = 1;

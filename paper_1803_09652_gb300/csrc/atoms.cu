@@ -329,6 +329,198 @@ __global__ void __launch_bounds__(256) k_mc_decide(MCArgs A) {
         }
 }
 
+// --- per-residue sweep (Sec. III.A.2) ---------------------------------------------
+// Every site of the requested kind gets one attempt, the sites taken in a
+// uniformly random order; each attempt is the one above, with the charges
+// left by the attempts before it.  Visit i of replica r draws Philox4x64-10,
+// key (seed, 0), counter (r, step, 5 + kind, i): word 0 picks the next site
+// among those not yet visited (a Fisher-Yates step over the sites of the kind
+// in index order), word 1 the new state, word 2 gives u.  The site rows are
+// computed once for all site atoms of the kind (k_sweep_rows, per slice as in
+// k_mc_rows); after an accepted move the rows of every listed atom m change
+// by sum_a dq_a A_ma, which k_sweep_decide adds before the next visit.
+
+struct SweepList {
+    int n_sites, n_atoms;
+    int site[SWEEP_MAX_SITES];           // global site index, in index order
+    int first[SWEEP_MAX_SITES + 1];      // its atoms are atom[first[k] .. first[k+1])
+    int atom[SWEEP_MAX_SITE_ATOMS];      // replica-local atom index
+};
+
+// Built by the whole block; false (for every thread) when replica r's sites
+// of the kind exceed the limits.
+__device__ bool sweep_list(const MCArgs& A, int r, SweepList& L) {
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        int ns = 0, na = 0, ok = 1;
+        for (int s = A.site_off[r]; s < A.site_off[r + 1] && ok; ++s) {
+            if (A.site_kind[s] != A.kind) continue;
+            const int n_s = A.site_atom_off[s + 1] - A.site_atom_off[s];
+            if (ns >= SWEEP_MAX_SITES || na + n_s > SWEEP_MAX_SITE_ATOMS || n_s > MC_MAX_SITE_ATOMS || n_s < 1) {
+                ok = 0;
+                break;
+            }
+            L.site[ns] = s;
+            L.first[ns] = na;
+            ++ns;
+            na += n_s;
+        }
+        L.n_sites = ns;
+        L.n_atoms = na;
+        L.first[ns] = na;
+        s_ok = ok;
+        if (!ok && A.err) atomicCAS(A.err, 0, GB_ERR_INVALID_ARG);
+    }
+    __syncthreads();
+    if (!s_ok) return false;
+    for (int k = 0; k < L.n_sites; ++k) {
+        const int a0 = A.site_atom_off[L.site[k]];
+        for (int a = threadIdx.x; a < L.first[k + 1] - L.first[k]; a += blockDim.x)
+            L.atom[L.first[k] + a] = A.site_atom_idx[a0 + a];
+    }
+    __syncthreads();
+    return true;
+}
+
+__global__ void __launch_bounds__(256) k_sweep_rows(MCArgs A) {
+    pdl_enter();
+    __shared__ SweepList L;
+    const int r = blockIdx.y, part = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+    if (!sweep_list(A, r, L) || L.n_sites == 0) return;
+    const int64_t base = A.atom_off[r];
+    const int n = (int)(A.atom_off[r + 1] - base);
+    const int j0 = part * MC_CHUNK, j1 = min(n, j0 + MC_CHUNK);
+    const float tke = (float)A.tau_ke, kc = (float)A.kc;
+    double* out = A.phi_part + ((size_t)r * A.n_parts + part) * SWEEP_MAX_SITE_ATOMS;
+    for (int k = wid; k < L.n_atoms; k += nw) {
+        const int lk = L.atom[k];
+        const int64_t gk = base + lk;
+        const float4 xk = A.xyzq[gk];
+        const float2 Rk = mc_Rh(A, gk);
+        double acc = 0.0;
+        for (int j = j0 + lane; j < j1; j += 32) {
+            const int64_t gj = base + j;
+            const float4 xj = A.xyzq[gj];
+            const float term = (j == lk) ? -tke / Rk.x : mc_pair_term(xk, Rk, xj, mc_Rh(A, gj), tke, kc);
+            acc += (double)(xj.w * term);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) out[k] = acc;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_sweep_decide(MCArgs A) {
+    pdl_enter();
+    __shared__ SweepList L;
+    __shared__ double s_phi[SWEEP_MAX_SITE_ATOMS];
+    __shared__ double s_dq[MC_MAX_SITE_ATOMS];
+    __shared__ int s_order[SWEEP_MAX_SITES];
+    __shared__ double sh[32];
+    __shared__ int s_li, s_site, s_nxt, s_acc;
+    const int r = blockIdx.x;
+    const int tid = threadIdx.x;
+    // every site of the replica starts as "not visited"
+    for (int s = A.site_off[r] + tid; s < A.site_off[r + 1]; s += blockDim.x) {
+        if (A.dG_out) A.dG_out[s] = 0.0;
+        if (A.acc_out) A.acc_out[s] = 2;
+    }
+    if (!sweep_list(A, r, L) || L.n_sites == 0) return;
+    const int64_t base = A.atom_off[r];
+    const int n = (int)(A.atom_off[r + 1] - base);
+    const int n_parts_r = (n + MC_CHUNK - 1) / MC_CHUNK;
+    for (int k = tid; k < L.n_atoms; k += blockDim.x) {
+        double phi = 0.0;
+        for (int p = 0; p < n_parts_r; ++p)
+            phi += A.phi_part[((size_t)r * A.n_parts + p) * SWEEP_MAX_SITE_ATOMS + k];
+        s_phi[k] = phi;
+    }
+    for (int k = tid; k < L.n_sites; k += blockDim.x) s_order[k] = k;
+    __syncthreads();
+    const u64 step = (A.ctr ? A.ctr[0] : 0) + A.step;
+    const float tke = (float)A.tau_ke, kc = (float)A.kc;
+    double u = 0.0;
+    int cur = 0;
+    for (int i = 0; i < L.n_sites; ++i) {
+        if (tid == 0) {
+            const Philox4 w = philox4x64((u64)r, step, 5 + (u64)A.kind, (u64)i, A.seed, 0);
+            const int j = i + pick_int(w.w[0], L.n_sites - i);
+            const int t = s_order[i];
+            s_order[i] = s_order[j];
+            s_order[j] = t;
+            s_li = s_order[i];
+            s_site = L.site[s_li];
+            cur = A.state[s_site];
+            const int k = pick_int(w.w[1], A.site_nstates[s_site] - 1);
+            s_nxt = (k < cur) ? k : k + 1;
+            u = unif53(w.w[2]);
+        }
+        __syncthreads();
+        const int li = s_li, site = s_site, nxt = s_nxt;
+        const int a0 = L.first[li], na = L.first[li + 1] - a0;
+        const int qo = A.site_q_off[site] + nxt * na;
+        for (int a = tid; a < na; a += blockDim.x)
+            s_dq[a] = (double)A.q_state[qo + a] - (double)A.xyzq[base + L.atom[a0 + a]].w;
+        __syncthreads();
+        double part = 0.0;
+        for (int t = tid; t < na * na; t += blockDim.x) {
+            const int k = t / na, l = t % na;
+            const int64_t gk = base + L.atom[a0 + k];
+            const float2 Rk = mc_Rh(A, gk);
+            float Akl;
+            if (k == l) {
+                Akl = -tke / Rk.x;
+                part += s_dq[k] * s_phi[a0 + k];
+            } else {
+                const int64_t gl = base + L.atom[a0 + l];
+                Akl = mc_pair_term(A.xyzq[gk], Rk, A.xyzq[gl], mc_Rh(A, gl), tke, kc);
+            }
+            part += 0.5 * s_dq[k] * s_dq[l] * (double)Akl;
+        }
+        const double dE = block_sum_d(part, sh);
+        if (tid == 0) {
+            const int so = A.site_state_off[site];
+            double dG = dE - (A.G_ref[so + nxt] - A.G_ref[so + cur]);
+            dG += FARADAY * (A.E[r] - A.E0_ref[site]) * (double)(A.n_e[so + nxt] - A.n_e[so + cur]);
+            dG += A.kT * LN10 * (A.pH[r] - A.pKa_ref[site]) * (double)(A.n_H[so + nxt] - A.n_H[so + cur]);
+            const int acc = (dG <= 0.0) || (u < exp(-dG / A.kT));
+            if (A.dG_out) A.dG_out[site] = dG;
+            if (A.acc_out) A.acc_out[site] = (uint8_t)acc;
+            if (acc) A.state[site] = nxt;
+            s_acc = acc;
+        }
+        __syncthreads();
+        if (s_acc) {
+            // rows of every listed atom: phi_m += sum_a dq_a A_ma (charges still old here)
+            for (int m = tid; m < L.n_atoms; m += blockDim.x) {
+                const int64_t gm = base + L.atom[m];
+                const float4 xm = A.xyzq[gm];
+                const float2 Rm = mc_Rh(A, gm);
+                double d = 0.0;
+                for (int a = 0; a < na; ++a) {
+                    const int64_t ga = base + L.atom[a0 + a];
+                    const float Ama = (ga == gm) ? -tke / Rm.x : mc_pair_term(xm, Rm, A.xyzq[ga], mc_Rh(A, ga), tke, kc);
+                    d += s_dq[a] * (double)Ama;
+                }
+                s_phi[m] += d;
+            }
+            __syncthreads();
+            for (int a = tid; a < na; a += blockDim.x) A.xyzq[base + L.atom[a0 + a]].w = A.q_state[qo + a];
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_mc_sweep(const MCArgs& a, int32_t M, cudaStream_t s) {
+    if (M == 0) return cudaSuccess;
+    if (a.n_parts > 0) {
+        const cudaError_t e = launch_pdl(k_sweep_rows, dim3((unsigned)a.n_parts, (unsigned)M), dim3(256), 0, s, a);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_pdl(k_sweep_decide, dim3(M), dim3(256), 0, s, a);
+}
+
 // --- replica exchange (Eq. 14, 15; schedule of Sec. III.B) ----------------------------
 __device__ __forceinline__ void exchange_pair(int32_t* rep_at_slot, const double* values,
                                               const int32_t* n_count, double c, int l, int len,

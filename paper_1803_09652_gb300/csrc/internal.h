@@ -138,9 +138,16 @@ struct MCArgs {
     int32_t* state;
     double* dG_out;
     uint8_t* acc_out;
-    double* phi_part;          // [M][n_parts][MC_MAX_SITE_ATOMS] slice partials (workspace)
+    double* phi_part;          // [M][n_parts][MC_MAX_SITE_ATOMS] slice partials (workspace;
+                               // [M][n_parts][SWEEP_MAX_SITE_ATOMS] for sweeps)
     int32_t n_parts;           // slices of the largest replica
+    int* err;                  // device error word (sweeps over their limits)
 };
+
+// Per-residue sweeps (Sec. III.A.2): limits per replica and kind.
+constexpr int SWEEP_MAX_SITE_ATOMS = 1024;
+constexpr int SWEEP_MAX_SITES = 256;
+cudaError_t launch_mc_sweep(const MCArgs& a, int32_t M, cudaStream_t s);
 
 cudaError_t launch_mc(const MCArgs& a, int32_t M, cudaStream_t s);
 
