@@ -29,16 +29,17 @@ LN10 = 2.302585092994045684
 class Params(C.Structure):
     _fields_ = [(k, C.c_double) for k in (
         "alpha", "beta", "gamma", "offset", "eps_in", "eps_out",
-        "bond_k", "bond_r0", "rep_k", "rep_sigma", "dt", "friction", "mass", "kT")]
+        "bond_k", "bond_r0", "rep_k", "rep_sigma", "dt", "friction", "mass", "kT", "kappa")]
 
 
 def default_params(**kw) -> Params:
     """OBC parameters alpha, beta, gamma = 1.0, 0.8, 4.85, offset 0.09 A,
-    eps_in 1, eps_out 78.5, no salt; MD driver constants (bond k 300 about
-    1.5 A, soft repulsion k 10 below 2.5 A, 2 fs, 10 / ps, 12 amu, 300 K)."""
+    eps_in 1, eps_out 78.5, no salt (kappa = 0); MD driver constants (bond k
+    300 about 1.5 A, soft repulsion k 10 below 2.5 A, 2 fs, 10 / ps, 12 amu,
+    300 K)."""
     d = dict(alpha=1.0, beta=0.8, gamma=4.85, offset=0.09, eps_in=1.0, eps_out=78.5,
              bond_k=300.0, bond_r0=1.5, rep_k=10.0, rep_sigma=2.5, dt=0.002, friction=10.0,
-             mass=12.0, kT=KB * 300.0)
+             mass=12.0, kT=KB * 300.0, kappa=0.0)
     d.update(kw)
     return Params(**d)
 

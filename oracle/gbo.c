@@ -47,6 +47,7 @@ typedef struct {
     double bond_k, bond_r0;         /* E = k (r - r0)^2 over (i, i+1) */
     double rep_k, rep_sigma;        /* E = k (sigma - r)^2, r < sigma, |i-j|>1 */
     double dt, friction, mass, kT;  /* Langevin driver */
+    double kappa;                   /* inverse Debye length of the salt (1/A); 0 = no salt */
 } gbo_params;
 
 /* ------------------------------------------------------------------------ */
@@ -196,23 +197,37 @@ static double f_gb(double r, double Ri, double Rj) {
     return sqrt(r * r + Ri * Rj * exp(-r * r / (4.0 * Ri * Rj)));
 }
 
+/* Solvent term of the GB kernel with Debye-Hueckel screening by salt (inverse
+ * Debye length kappa; kappa = 0 gives the plain form):
+ *   g(f) = (1/eps_in - exp(-kappa f) / eps_out) / f,
+ * so that E_GB = -1/2 k_e sum_i sum_j q_i q_j g(f_ij) with f_ii = R_i, and its
+ * derivative g'(f) = -(1/eps_in - exp(-kappa f)/eps_out) / f^2
+ *                    + kappa exp(-kappa f) / (eps_out f). */
+static double gb_g(double f, const gbo_params* p) {
+    return (1.0 / p->eps_in - exp(-p->kappa * f) / p->eps_out) / f;
+}
+static double gb_dg(double f, const gbo_params* p) {
+    double e = exp(-p->kappa * f);
+    return -(1.0 / p->eps_in - e / p->eps_out) / (f * f) + p->kappa * e / (p->eps_out * f);
+}
+
 /* Electrostatic energy at fixed Born radii:
- *   E_GB   = -1/2 (1/eps_in - 1/eps_out) k_e sum_i sum_j q_i q_j / f_ij   (f_ii = R_i)
+ *   E_GB   = -1/2 k_e sum_i sum_j q_i q_j g(f_ij)   (f_ii = R_i; g above: 
+ *            (1/eps_in - 1/eps_out) / f without salt)
  *   E_Coul = (k_e / eps_in) sum_{i<j} q_i q_j / r_ij
  * E[0] = E_GB, E[1] = E_Coul. */
 void gbo_energy_fixed_radii(int64_t n, const double* x, const double* q, const double* R,
                             const gbo_params* p, double E[2]) {
-    double tau = 1.0 / p->eps_in - 1.0 / p->eps_out;
     double egb = 0.0, ecoul = 0.0;
     for (int64_t i = 0; i < n; ++i) {
         for (int64_t j = 0; j < n; ++j) {
             if (j == i) {
-                egb += -0.5 * tau * GBO_KE * q[i] * q[i] / R[i];
+                egb += -0.5 * GBO_KE * q[i] * q[i] * gb_g(R[i], p);
                 continue;
             }
             double d[3];
             double r = dist(x, i, j, d);
-            egb += -0.5 * tau * GBO_KE * q[i] * q[j] / f_gb(r, R[i], R[j]);
+            egb += -0.5 * GBO_KE * q[i] * q[j] * gb_g(f_gb(r, R[i], R[j]), p);
             if (j > i) ecoul += (GBO_KE / p->eps_in) * q[i] * q[j] / r;
         }
     }
@@ -230,17 +245,16 @@ void gbo_energy_forces(int64_t n, const double* x, const double* q, const double
     double* dRdpsi = (double*)malloc(sizeof(double) * (size_t)n);
     double* dEdR = (double*)calloc((size_t)n, sizeof(double));
     gbo_born_radii(n, x, rho, screen, p, NULL, NULL, R, dRdpsi);
-    double tau = 1.0 / p->eps_in - 1.0 / p->eps_out;
     double kc = GBO_KE / p->eps_in;
     double egb = 0.0, ecoul = 0.0;
     if (F) memset(F, 0, sizeof(double) * 3 * (size_t)n);
     if (phi) memset(phi, 0, sizeof(double) * (size_t)n);
 
-    /* direct part: ordered pairs (i, j), each carrying -1/2 tau k_e q_i q_j / f_ij */
+    /* direct part: ordered pairs (i, j), each carrying -1/2 k_e q_i q_j g(f_ij) */
     for (int64_t i = 0; i < n; ++i) {
-        egb += -0.5 * tau * GBO_KE * q[i] * q[i] / R[i];
-        dEdR[i] += 0.5 * tau * GBO_KE * q[i] * q[i] / (R[i] * R[i]);
-        if (phi) phi[i] += -tau * GBO_KE * q[i] / R[i];
+        egb += -0.5 * GBO_KE * q[i] * q[i] * gb_g(R[i], p);
+        dEdR[i] += -0.5 * GBO_KE * q[i] * q[i] * gb_dg(R[i], p);
+        if (phi) phi[i] += -GBO_KE * q[i] * gb_g(R[i], p);
         for (int64_t j = 0; j < n; ++j) {
             if (j == i) continue;
             double d[3];
@@ -249,14 +263,15 @@ void gbo_energy_forces(int64_t n, const double* x, const double* q, const double
             double D = r * r / (4.0 * RR);
             double e = exp(-D);
             double f = sqrt(r * r + RR * e);
-            double c = -0.5 * tau * GBO_KE * q[i] * q[j];
-            egb += c / f;
-            /* d(c/f) = -c/f^2 df, with df/dr = r (1 - e/4) / f,
+            double c = -0.5 * GBO_KE * q[i] * q[j];
+            egb += c * gb_g(f, p);
+            /* d(c g(f)) = c g'(f) df, with df/dr = r (1 - e/4) / f,
              * df/dR_i = R_j e (1 + D) / (2 f), df/dR_j = R_i e (1 + D) / (2 f) */
-            double dEdr = -c / (f * f) * r * (1.0 - 0.25 * e) / f;
-            dEdR[i] += -c / (f * f) * R[j] * e * (1.0 + D) / (2.0 * f);
-            dEdR[j] += -c / (f * f) * R[i] * e * (1.0 + D) / (2.0 * f);
-            if (phi) phi[i] += -tau * GBO_KE * q[j] / f + kc * q[j] / r;
+            double dEdf = c * gb_dg(f, p);
+            double dEdr = dEdf * r * (1.0 - 0.25 * e) / f;
+            dEdR[i] += dEdf * R[j] * e * (1.0 + D) / (2.0 * f);
+            dEdR[j] += dEdf * R[i] * e * (1.0 + D) / (2.0 * f);
+            if (phi) phi[i] += -GBO_KE * q[j] * gb_g(f, p) + kc * q[j] / r;
             if (j > i) {
                 ecoul += kc * q[i] * q[j] / r;
                 dEdr += -kc * q[i] * q[j] / (r * r);
