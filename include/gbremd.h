@@ -52,15 +52,20 @@ typedef struct gb_ctx gb_ctx;
  * Onufriev, Bashford and Case ("igb=2", Sec. III.D) for MD and for every
  * state-change energy; alpha, beta, gamma rescale the HCT integral into the
  * effective Born radius, `offset` is subtracted from each intrinsic radius,
- * eps_in / eps_out are the solute and solvent dielectric constants (no salt,
- * no cutoff).  rep_k, rep_sigma: optional soft repulsion
+ * eps_in / eps_out are the solute and solvent dielectric constants (no
+ * cutoff).  rep_k, rep_sigma: optional soft repulsion
  * rep_k (rep_sigma - r)^2 for r < rep_sigma between atoms more than one
- * position apart in the chain (0 disables it; MD driver only). */
+ * position apart in the chain (0 disables it; MD driver only).  kappa: inverse
+ * Debye length of dissolved salt (1/A; 0 = no salt, the paper's setting);
+ * the solvent term of every GB pair (and self) term is screened,
+ *   (1/eps_in - 1/eps_out) / f  ->  (1/eps_in - exp(-kappa f)/eps_out) / f,
+ * in energies, forces, dE/dq and the Monte Carlo energy changes. */
 typedef struct {
     float alpha, beta, gamma;
     float offset;
     float eps_in, eps_out;
     float rep_k, rep_sigma;
+    float kappa;
 } gb_params;
 
 /* Create a context for a fixed batch layout.

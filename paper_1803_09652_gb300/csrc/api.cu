@@ -230,6 +230,8 @@ gbk::PairArgs pair_args(const gb_ctx* c, const float* xyzq, const float* rad) {
     a.offset = c->p.offset;
     a.tau_ke = (float)((1.0 / c->p.eps_in - 1.0 / c->p.eps_out) * gbk::KE);
     a.kc = (float)(gbk::KE / c->p.eps_in);
+    a.ke_out = (float)(gbk::KE / c->p.eps_out);
+    a.kappa = c->p.kappa;
     a.rep_k = c->p.rep_k;
     a.rep_sigma = c->p.rep_sigma;
     a.I_acc = c->I_acc;
@@ -255,6 +257,9 @@ gbk::AtomArgs atom_args(const gb_ctx* c, const float* xyzq, const float* rad) {
     a.gamma = c->p.gamma;
     a.offset = c->p.offset;
     a.tau_ke = (1.0 / c->p.eps_in - 1.0 / c->p.eps_out) * gbk::KE;
+    a.kc = gbk::KE / c->p.eps_in;
+    a.ke_out = gbk::KE / c->p.eps_out;
+    a.kappa = c->p.kappa;
     a.I_acc = c->I_acc;
     a.dR_acc = c->dR_acc;
     a.phi_acc = c->phi_acc;
@@ -278,6 +283,7 @@ cudaError_t mark(gb_ctx* c, cudaEvent_t e, cudaStream_t s) {
 int evaluate(gb_ctx* c, const float* xyzq, const float* rad, float* R_out, int flags,
              double* phi_out, cudaStream_t s, const cudaEvent_t* ev = nullptr,
              const gbk::MDArgs* md = nullptr, bool build_boxes = true) {
+    if (c->p.kappa != 0.0f) flags |= gbk::EF_SALT;
     const gbk::PairArgs pa = pair_args(c, xyzq, rad);
     const gbk::AtomArgs aa = atom_args(c, xyzq, rad);
     if (build_boxes) GB_CHECK(c, gbk::launch_tile_boxes(pa, c->M, c->n_tiles32, s));
@@ -332,7 +338,8 @@ extern "C" int gb_ctx_create(gb_ctx** out, int32_t n_rep, const int64_t* atom_of
         if (atom_off[r + 1] < atom_off[r]) return fail(nullptr, GB_ERR_INVALID_ARG, "atom_off must be non-decreasing");
     if (atom_off[n_rep] >= (1LL << 31)) return fail(nullptr, GB_ERR_INVALID_ARG, "too many atoms");
     if (!(params->offset >= 0.0f) || !(params->eps_in > 0.0f) || !(params->eps_out > 0.0f) ||
-        !(params->rep_k >= 0.0f) || !(params->rep_sigma >= 0.0f))
+        !(params->rep_k >= 0.0f) || !(params->rep_sigma >= 0.0f) || !(params->kappa >= 0.0f) ||
+        !(params->kappa < 1.0e3f))
         return fail(nullptr, GB_ERR_INVALID_ARG, "invalid GB parameters");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
@@ -550,6 +557,8 @@ static gbk::MCArgs mc_args(const gb_ctx* c, const gb_sites* sites, float* xyzq, 
     a.kT = kT;
     a.tau_ke = (1.0 / c->p.eps_in - 1.0 / c->p.eps_out) * gbk::KE;
     a.kc = gbk::KE / c->p.eps_in;
+    a.ke_out = gbk::KE / c->p.eps_out;
+    a.kappa = c->p.kappa;
     a.seed = seed;
     a.step = step;
     a.ctr = nullptr;
@@ -715,6 +724,8 @@ int enqueue_mc(gb_ctx* c, gb_md_state* st, const gb_sites* sites, int64_t k, cud
         a.kT = st->kT;
         a.tau_ke = (1.0 / c->p.eps_in - 1.0 / c->p.eps_out) * gbk::KE;
         a.kc = gbk::KE / c->p.eps_in;
+        a.ke_out = gbk::KE / c->p.eps_out;
+        a.kappa = c->p.kappa;
         a.seed = st->seed;
         a.step = (u64)k;
         a.ctr = c->ctr;
@@ -775,7 +786,7 @@ int enqueue_steps(gb_ctx* c, gb_md_state* st, const gb_sites* sites, int64_t len
     const int flags = (c->p.rep_k != 0.0f) ? gbk::EF_REP : 0;
     auto mc_due = [&](int64_t t) { return sites && st->mc_every > 0 && t % st->mc_every == 0; };
     auto ex_due = [&](int64_t t) { return sites && st->grid && st->ex_every > 0 && t % st->ex_every == 0; };
-    if (c->use_persist && c->persist_grid > 0) {
+    if (c->use_persist && c->persist_grid > 0 && c->p.kappa == 0.0f) {
         gbk::PersistArgs a{};
         a.pa = pair_args(c, xyzq, rad);
         a.aa = aa;
@@ -986,7 +997,7 @@ extern "C" int gb_autotune(gb_ctx* c, const float* xyzq, const float* rad, void*
             for (int cap : caps) {
                 for (int k = 0; k < 3; ++k) c->tasks.cap[k] = cap;
                 float ms_min[3] = {1e30f, 1e30f, 1e30f};
-                for (int rep = 0; rep < 3 && !rc; ++rep) {
+                for (int rep = 0; rep < 5 && !rc; ++rep) {
                     rc = evaluate(c, xyzq, rad, nullptr, 0, nullptr, s, ev);
                     if (rc) break;
                     cudaEventSynchronize(ev[5]);

@@ -46,9 +46,10 @@ __global__ void k_energy_finalize(AtomArgs A, int want_energy, double* phi_out, 
         const int64_t g = base + i;
         double R;
         const double q = chain_factor_atom(A, g, &R);
-        eself = -0.5 * A.tau_ke * q * q / R;
+        const double tE = gb_screen(A.kc, A.ke_out, A.kappa, R).x;
+        eself = -0.5 * tE * q * q / R;
         if (phi_out) {
-            phi_out[g] = unfix(A.phi_acc[g]) - A.tau_ke * q / R;
+            phi_out[g] = unfix(A.phi_acc[g]) - tE * q / R;
             A.phi_acc[g] = 0;
         }
         if (bond_k != 0.0f) {
@@ -214,12 +215,21 @@ __device__ __forceinline__ float2 mc_Rh(const MCArgs& A, int64_t g) {
     return A.Rh[g];
 }
 
-__device__ __forceinline__ float mc_pair_term(float4 xk, float2 Rk, float4 xj, float2 Rj, float tke, float kc) {
+// A_kj = k_c / r - tE(f) / f, tE the (screened) solvent factor of gb_screen.
+__device__ __forceinline__ float mc_pair_term(float4 xk, float2 Rk, float4 xj, float2 Rj, float tke, float kc,
+                                              float ke_out, float kappa) {
     const float dx = xj.x - xk.x, dy = xj.y - xk.y, dz = xj.z - xk.z;
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     const float e = __expf(-r2 * (Rk.y * Rj.y));          // exp(-r^2 / (4 R_k R_j))
     const float f2 = fmaf(Rk.x * Rj.x, e, r2);
-    return kc * rsqrtf(r2) - tke * rsqrtf(f2);
+    const float finv = rsqrtf(f2);
+    const float t = (kappa == 0.0f) ? tke : kc - ke_out * __expf(-kappa * f2 * finv);
+    return kc * rsqrtf(r2) - t * finv;
+}
+// A_kk = -tE(R_k) / R_k
+__device__ __forceinline__ float mc_self_term(float Rk, float tke, float kc, float ke_out, float kappa) {
+    const float t = (kappa == 0.0f) ? tke : kc - ke_out * __expf(-kappa * Rk);
+    return -t / Rk;
 }
 
 __global__ void __launch_bounds__(256) k_mc_rows(MCArgs A) {
@@ -237,7 +247,7 @@ __global__ void __launch_bounds__(256) k_mc_rows(MCArgs A) {
     const int64_t base = A.atom_off[r];
     const int n = (int)(A.atom_off[r + 1] - base);
     const int j0 = part * MC_CHUNK, j1 = min(n, j0 + MC_CHUNK);
-    const float tke = (float)A.tau_ke, kc = (float)A.kc;
+    const float tke = (float)A.tau_ke, kc = (float)A.kc, keo = (float)A.ke_out, kap = (float)A.kappa;
     double* out = A.phi_part + ((size_t)r * A.n_parts + part) * MC_MAX_SITE_ATOMS;
     for (int k = wid; k < na; k += nw) {
         const int lk = A.site_atom_idx[a0 + k];
@@ -248,7 +258,7 @@ __global__ void __launch_bounds__(256) k_mc_rows(MCArgs A) {
         for (int j = j0 + lane; j < j1; j += 32) {
             const int64_t gj = base + j;
             const float4 xj = A.xyzq[gj];
-            const float term = (j == lk) ? -tke / Rk.x : mc_pair_term(xk, Rk, xj, mc_Rh(A, gj), tke, kc);
+            const float term = (j == lk) ? mc_self_term(Rk.x, tke, kc, keo, kap) : mc_pair_term(xk, Rk, xj, mc_Rh(A, gj), tke, kc, keo, kap);
             acc += (double)(xj.w * term);
         }
 #pragma unroll
@@ -291,7 +301,7 @@ __global__ void __launch_bounds__(256) k_mc_decide(MCArgs A) {
         s_phi[k] = phi;
     }
     __syncthreads();
-    const float tke = (float)A.tau_ke, kc = (float)A.kc;
+    const float tke = (float)A.tau_ke, kc = (float)A.kc, keo = (float)A.ke_out, kap = (float)A.kappa;
     double part = 0.0;
     for (int t = tid; t < na * na; t += blockDim.x) {
         const int k = t / na, l = t % na;
@@ -299,11 +309,11 @@ __global__ void __launch_bounds__(256) k_mc_decide(MCArgs A) {
         const float2 Rk = mc_Rh(A, gk);
         float Akl;
         if (k == l) {
-            Akl = -tke / Rk.x;
+            Akl = mc_self_term(Rk.x, tke, kc, keo, kap);
             part += s_dq[k] * s_phi[k];
         } else {
             const int64_t gl = base + A.site_atom_idx[a0 + l];
-            Akl = mc_pair_term(A.xyzq[gk], Rk, A.xyzq[gl], mc_Rh(A, gl), tke, kc);
+            Akl = mc_pair_term(A.xyzq[gk], Rk, A.xyzq[gl], mc_Rh(A, gl), tke, kc, keo, kap);
         }
         part += 0.5 * s_dq[k] * s_dq[l] * (double)Akl;
     }
@@ -391,7 +401,7 @@ __global__ void __launch_bounds__(256) k_sweep_rows(MCArgs A) {
     const int64_t base = A.atom_off[r];
     const int n = (int)(A.atom_off[r + 1] - base);
     const int j0 = part * MC_CHUNK, j1 = min(n, j0 + MC_CHUNK);
-    const float tke = (float)A.tau_ke, kc = (float)A.kc;
+    const float tke = (float)A.tau_ke, kc = (float)A.kc, keo = (float)A.ke_out, kap = (float)A.kappa;
     double* out = A.phi_part + ((size_t)r * A.n_parts + part) * SWEEP_MAX_SITE_ATOMS;
     for (int k = wid; k < L.n_atoms; k += nw) {
         const int lk = L.atom[k];
@@ -402,7 +412,7 @@ __global__ void __launch_bounds__(256) k_sweep_rows(MCArgs A) {
         for (int j = j0 + lane; j < j1; j += 32) {
             const int64_t gj = base + j;
             const float4 xj = A.xyzq[gj];
-            const float term = (j == lk) ? -tke / Rk.x : mc_pair_term(xk, Rk, xj, mc_Rh(A, gj), tke, kc);
+            const float term = (j == lk) ? mc_self_term(Rk.x, tke, kc, keo, kap) : mc_pair_term(xk, Rk, xj, mc_Rh(A, gj), tke, kc, keo, kap);
             acc += (double)(xj.w * term);
         }
 #pragma unroll
@@ -439,7 +449,7 @@ __global__ void __launch_bounds__(256) k_sweep_decide(MCArgs A) {
     for (int k = tid; k < L.n_sites; k += blockDim.x) s_order[k] = k;
     __syncthreads();
     const u64 step = (A.ctr ? A.ctr[0] : 0) + A.step;
-    const float tke = (float)A.tau_ke, kc = (float)A.kc;
+    const float tke = (float)A.tau_ke, kc = (float)A.kc, keo = (float)A.ke_out, kap = (float)A.kappa;
     double u = 0.0;
     int cur = 0;
     for (int i = 0; i < L.n_sites; ++i) {
@@ -470,11 +480,11 @@ __global__ void __launch_bounds__(256) k_sweep_decide(MCArgs A) {
             const float2 Rk = mc_Rh(A, gk);
             float Akl;
             if (k == l) {
-                Akl = -tke / Rk.x;
+                Akl = mc_self_term(Rk.x, tke, kc, keo, kap);
                 part += s_dq[k] * s_phi[a0 + k];
             } else {
                 const int64_t gl = base + L.atom[a0 + l];
-                Akl = mc_pair_term(A.xyzq[gk], Rk, A.xyzq[gl], mc_Rh(A, gl), tke, kc);
+                Akl = mc_pair_term(A.xyzq[gk], Rk, A.xyzq[gl], mc_Rh(A, gl), tke, kc, keo, kap);
             }
             part += 0.5 * s_dq[k] * s_dq[l] * (double)Akl;
         }
@@ -500,7 +510,7 @@ __global__ void __launch_bounds__(256) k_sweep_decide(MCArgs A) {
                 double d = 0.0;
                 for (int a = 0; a < na; ++a) {
                     const int64_t ga = base + L.atom[a0 + a];
-                    const float Ama = (ga == gm) ? -tke / Rm.x : mc_pair_term(xm, Rm, A.xyzq[ga], mc_Rh(A, ga), tke, kc);
+                    const float Ama = (ga == gm) ? mc_self_term(Rm.x, tke, kc, keo, kap) : mc_pair_term(xm, Rm, A.xyzq[ga], mc_Rh(A, ga), tke, kc, keo, kap);
                     d += s_dq[a] * (double)Ama;
                 }
                 s_phi[m] += d;

@@ -40,12 +40,23 @@ __device__ __forceinline__ void born_finalize_atom(const AtomArgs& A, int64_t g,
     if (R_out) R_out[g] = R;
 }
 
+// Screened solvent factors at distance f (FP64): with ek = exp(-kappa f),
+//   tE = k_e (1/eps_in - ek/eps_out)              (GB term -1/2 q q tE / f)
+//   tF = k_e (1/eps_in - ek (1 + kappa f)/eps_out)  (d/df (tE/f) = -tF / f^2);
+// both equal (1/eps_in - 1/eps_out) k_e without salt.
+__device__ __forceinline__ double2 gb_screen(double kc, double ke_out, double kappa, double f) {
+    if (kappa == 0.0) return make_double2(kc - ke_out, kc - ke_out);
+    const double ek = exp(-kappa * f);
+    return make_double2(kc - ke_out * ek, kc - ke_out * ek * (1.0 + kappa * f));
+}
+
 // Chain factor c = dE/dR * a dR/dpsi of atom g from the pair part of dE/dR
-// (cleared here) plus the self term 1/2 tau k_e q^2 / R^2.  Returns q.
+// (cleared here) plus the self term 1/2 tF(R) q^2 / R^2.  Returns q.
 __device__ __forceinline__ double chain_factor_atom(const AtomArgs& A, int64_t g, double* R_used) {
     const double q = __ldcg(&A.xyzq[g]).w;
     const double R = __ldcg(&A.Rh[g]).x;
-    const double dEdR = unfix(__ldcg(&A.dR_acc[g])) + 0.5 * A.tau_ke * q * q / (R * R);
+    const double2 t = gb_screen(A.kc, A.ke_out, A.kappa, R);
+    const double dEdR = unfix(__ldcg(&A.dR_acc[g])) + 0.5 * t.y * q * q / (R * R);
     A.dR_acc[g] = 0;
     A.cc[g] = (float)(dEdR * (double)__ldcg(&A.cfac[g]));
     *R_used = R;

@@ -19,6 +19,7 @@ struct PairArgs {
     const float* cc;           // chain factor c_i   (pass 3)
     float offset;
     float tau_ke;              // (1/eps_in - 1/eps_out) k_e
+    float ke_out, kappa;       // k_e / eps_out and the salt's inverse Debye length (EF_SALT)
     float kc;                  // k_e / eps_in
     float rep_k, rep_sigma;    // soft repulsion (rep_k == 0: off)
     u64* I_acc;                // [N]   Born integrals, 2^40 fixed point
@@ -45,7 +46,7 @@ struct TaskList {
 enum PassKind { PASS_BORN = 0, PASS_ENERGY = 1, PASS_CHAIN = 2 };
 
 // flags for the energy pass
-enum { EF_ENERGY = 1, EF_PHI = 2, EF_REP = 4 };
+enum { EF_ENERGY = 1, EF_PHI = 2, EF_REP = 4, EF_SALT = 8 };
 
 cudaError_t launch_pairs(int pass, int flags, const PairArgs& a, const TaskList& t,
                          int warps_per_block, cudaStream_t s);
@@ -65,6 +66,7 @@ struct AtomArgs {
     const float2* rad;
     float alpha, beta, gamma, offset;
     double tau_ke;
+    double kc, ke_out, kappa;  // k_e / eps_in, k_e / eps_out, salt (self terms)
     u64* I_acc;
     u64* dR_acc;
     u64* phi_acc;
@@ -131,6 +133,7 @@ struct MCArgs {
     const double* E;
     double kT;
     double tau_ke, kc;
+    double ke_out, kappa;      // salt screening of the solvent term (kappa 0: none)
     u64 seed;
     u64 step;
     const u64* ctr;            // when non-null the step is ctr[0] + step

@@ -97,7 +97,8 @@ extern "C" int gb_energy_forces_static(int32_t n_atoms, const gb_params* params,
     if (!params || !xyzq || !rad_screen) return GB_ERR_INVALID_ARG;
     if (!R_out && !F_fixed && !F_out && !E_out && !dEdq_out) return GB_ERR_INVALID_ARG;
     if (((uintptr_t)xyzq % 16) || ((uintptr_t)rad_screen % 8)) return GB_ERR_INVALID_ARG;
-    if (!(params->eps_in > 0.0f) || !(params->eps_out > 0.0f) || !(params->offset >= 0.0f))
+    if (!(params->eps_in > 0.0f) || !(params->eps_out > 0.0f) || !(params->offset >= 0.0f) ||
+        !(params->kappa >= 0.0f) || !(params->kappa < 1.0e3f))
         return GB_ERR_INVALID_ARG;
     unsigned char* base = nullptr;
     int rc = scratch_for_current_device(&base);
@@ -135,6 +136,8 @@ extern "C" int gb_energy_forces_static(int32_t n_atoms, const gb_params* params,
     pa.offset = params->offset;
     pa.tau_ke = (float)((1.0 / params->eps_in - 1.0 / params->eps_out) * gbk::KE);
     pa.kc = (float)(gbk::KE / params->eps_in);
+    pa.ke_out = (float)(gbk::KE / params->eps_out);
+    pa.kappa = params->kappa;
     pa.rep_k = params->rep_k;
     pa.rep_sigma = params->rep_sigma;
     pa.I_acc = I_acc;
@@ -155,6 +158,9 @@ extern "C" int gb_energy_forces_static(int32_t n_atoms, const gb_params* params,
     aa.gamma = params->gamma;
     aa.offset = params->offset;
     aa.tau_ke = (1.0 / params->eps_in - 1.0 / params->eps_out) * gbk::KE;
+    aa.kc = gbk::KE / params->eps_in;
+    aa.ke_out = gbk::KE / params->eps_out;
+    aa.kappa = params->kappa;
     aa.I_acc = I_acc;
     aa.dR_acc = dR_acc;
     aa.phi_acc = phi_acc;
@@ -170,7 +176,7 @@ extern "C" int gb_energy_forces_static(int32_t n_atoms, const gb_params* params,
     tl.d_tasks = tasks;
     tl.n_tasks = n_tasks;
     const int flags = (E_out ? gbk::EF_ENERGY : 0) | (dEdq_out ? gbk::EF_PHI : 0) |
-                      (params->rep_k != 0.0f ? gbk::EF_REP : 0);
+                      (params->rep_k != 0.0f ? gbk::EF_REP : 0) | (params->kappa != 0.0f ? gbk::EF_SALT : 0);
     const int wpb = 8;
     if (gbk::launch_pairs(gbk::PASS_BORN, 0, pa, tl, wpb, s) != cudaSuccess) return GB_ERR_CUDA;
     if (gbk::launch_born_finalize(aa, R_out, s) != cudaSuccess) return GB_ERR_CUDA;

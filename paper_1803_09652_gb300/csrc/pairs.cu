@@ -45,7 +45,7 @@ cudaError_t launch_pairs(int pass, int flags, const PairArgs& a, const TaskList&
     const int cap = t.cap[pass];
     if (pass == PASS_BORN) return go<Born, 0>(a, t, cap, wpb, s);
     if (pass == PASS_CHAIN) return go<Chain, 0>(a, t, cap, wpb, s);
-    switch (flags & 7) {
+    switch (flags & 15) {
         case 0: return go<EnergyF<0>, 0>(a, t, cap, wpb, s);
         case 1: return go<EnergyF<1>, 1>(a, t, cap, wpb, s);
         case 2: return go<EnergyF<2>, 2>(a, t, cap, wpb, s);
@@ -53,7 +53,15 @@ cudaError_t launch_pairs(int pass, int flags, const PairArgs& a, const TaskList&
         case 4: return go<EnergyF<4>, 4>(a, t, cap, wpb, s);
         case 5: return go<EnergyF<5>, 5>(a, t, cap, wpb, s);
         case 6: return go<EnergyF<6>, 6>(a, t, cap, wpb, s);
-        default: return go<EnergyF<7>, 7>(a, t, cap, wpb, s);
+        case 7: return go<EnergyF<7>, 7>(a, t, cap, wpb, s);
+        case 8: return go<EnergyF<8>, 8>(a, t, cap, wpb, s);
+        case 9: return go<EnergyF<9>, 9>(a, t, cap, wpb, s);
+        case 10: return go<EnergyF<10>, 10>(a, t, cap, wpb, s);
+        case 11: return go<EnergyF<11>, 11>(a, t, cap, wpb, s);
+        case 12: return go<EnergyF<12>, 12>(a, t, cap, wpb, s);
+        case 13: return go<EnergyF<13>, 13>(a, t, cap, wpb, s);
+        case 14: return go<EnergyF<14>, 14>(a, t, cap, wpb, s);
+        default: return go<EnergyF<15>, 15>(a, t, cap, wpb, s);
     }
 }
 

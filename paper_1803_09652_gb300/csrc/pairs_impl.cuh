@@ -62,12 +62,26 @@ __device__ __forceinline__ float ex2_ftz(float x) {
 }
 __device__ __forceinline__ f2 rsqrt2(f2 x) { return make_float2(rsqrt_ftz(x.x), rsqrt_ftz(x.y)); }
 __device__ __forceinline__ f2 ex22(f2 x) { return make_float2(ex2_ftz(x.x), ex2_ftz(x.y)); }
+// 1/sqrt(x) refined by one Newton step y (3 - x y^2) / 2
+__device__ __forceinline__ f2 rsqrt2_nr(f2 x) {
+    const f2 y = rsqrt2(x);
+    return mul2(y, fma2(F2(-0.5f), mul2(x, mul2(y, y)), F2(1.5f)));
+}
 
 constexpr float SQRT_LOG2E = 1.2011224087864498f;  // sqrt(log2(e))
 constexpr float LN2 = 0.69314718055994531f;
+constexpr float LOG2E = 1.4426950408889634f;
 constexpr float FAR_R2 = 1.0e30f;                  // r^2 given to masked-off lanes
 
 __device__ __forceinline__ f2 neg2(f2 v) { return make_float2(-v.x, -v.y); }
+// Compensated summation (Kahan): sum + c carries the running total, with c
+// the negated rounding error of the additions so far.
+__device__ __forceinline__ void kahan_add(f2& sum, f2& c, f2 term) {
+    const f2 y = add2(term, neg2(c));
+    const f2 t = add2(sum, y);
+    c = add2(add2(t, neg2(sum)), neg2(y));
+    sum = t;
+}
 // Reciprocal: MUFU estimate (flush-to-zero; arguments here are O(1) lengths)
 // and one Newton step y + y (1 - x y), which brings it to about half an ulp.
 __device__ __forceinline__ float rcp_ftz(float x) {
@@ -306,8 +320,9 @@ struct Energy {
     struct JState { float x, y, z, q, R, h, fx, fy, fz, dR, phi; };
     struct Part {
         f2 sx, sy, sz, dR, phi, egb, ec, er;   // s* = sum of fr d (the i force is -s)
+        f2 kgb, kc, kr;                        // compensation terms of the energy sums
         __device__ __forceinline__ void zero() {
-            sx = sy = sz = dR = phi = egb = ec = er = F2(0.0f);
+            sx = sy = sz = dR = phi = egb = ec = er = kgb = kc = kr = F2(0.0f);
         }
     };
     static __device__ __forceinline__ void load_one(const PairArgs& A, int64_t base, int n, int i, float& x,
@@ -337,14 +352,29 @@ struct Energy {
                                                 const BlockInfo&, int i0, int jbase, int k) {
         const f2 dx = add2(F2(j.x), i.nx), dy = add2(F2(j.y), i.ny), dz = add2(F2(j.z), i.nz);
         const f2 r2 = safe_r2<MODE>(fma2(dx, dx, fma2(dy, dy, mul2(dz, dz))), m);
-        const f2 rinv = rsqrt2(r2);
+        // energies are sums of large terms that cancel: when they are wanted,
+        // one Newton step takes the MUFU reciprocal square roots to FP32 rounding
+        const f2 rinv = (FLAGS & EF_ENERGY) ? rsqrt2_nr(r2) : rsqrt2(r2);
         const f2 rinv2 = mul2(rinv, rinv);
         const f2 qq = mul2(i.q, F2(j.q));
         const f2 nDl = mul2(r2, mul2(i.nh, F2(j.h)));                 // -D log2(e)
         const f2 e = ex22(nDl);                                       // exp(-D)
-        const f2 finv = rsqrt2(fma2(mul2(i.R, F2(j.R)), e, r2));
+        const f2 fsq = fma2(mul2(i.R, F2(j.R)), e, r2);
+        const f2 finv = (FLAGS & EF_ENERGY) ? rsqrt2_nr(fsq) : rsqrt2(fsq);
         const f2 finv3 = mul2(mul2(finv, finv), finv);
-        const f2 w = mul2(mul2(qq, F2(0.5f * A.tau_ke)), finv3);      // tau k_e q q / (2 f^3)
+        // solvent factors: tE in the energy (-tE q q / f), tF in its f-derivative;
+        // both (1/eps_in - 1/eps_out) k_e without salt, screened by
+        // exp(-kappa f) with it (Debye-Hueckel)
+        f2 tE = F2(A.tau_ke), w;
+        if (FLAGS & EF_SALT) {
+            const f2 f = mul2(fsq, finv);
+            const f2 ekv = mul2(F2(A.ke_out), ex22(mul2(F2(-A.kappa * LOG2E), f)));   // k_e e^{-kappa f} / eps_out
+            tE = add2(F2(A.kc), neg2(ekv));
+            const f2 tF = fma2(neg2(ekv), mul2(F2(A.kappa), f), tE);
+            w = mul2(mul2(qq, F2(0.5f)), mul2(tF, finv3));           // tF q q / (2 f^3)
+        } else {
+            w = mul2(mul2(qq, F2(0.5f * A.tau_ke)), finv3);
+        }
         const f2 nu = fma2(F2(0.5f), e, F2(-2.0f));                   // -2 (1 - e/4)
         const f2 qc = mul2(qq, F2(A.kc));
         f2 fr = fma2(qc, mul2(rinv2, rinv), mul2(w, nu));
@@ -377,14 +407,16 @@ struct Energy {
         p.dR = fma2(G, F2(j.R), p.dR);
         j.dR = fmaf(G.y, i.R.y, fmaf(G.x, i.R.x, j.dR));
         if (FLAGS & EF_PHI) {
-            const f2 P = keep<MODE>(fma2(F2(-A.tau_ke), finv, mul2(F2(A.kc), rinv)), m);
+            const f2 P = keep<MODE>(fma2(neg2(tE), finv, mul2(F2(A.kc), rinv)), m);
             p.phi = fma2(P, F2(j.q), p.phi);
             j.phi = fmaf(P.y, i.q.y, fmaf(P.x, i.q.x, j.phi));
         }
         if (FLAGS & EF_ENERGY) {
-            p.egb = add2(p.egb, keep<MODE>(mul2(F2(-A.tau_ke), mul2(qq, finv)), m));
-            p.ec = add2(p.ec, keep<MODE>(mul2(qc, rinv), m));
-            if (FLAGS & EF_REP) p.er = add2(p.er, keep<MODE>(er, m));
+            // the pair energies are large terms that cancel: compensated
+            // (Kahan) FP32 sums within the block
+            kahan_add(p.egb, p.kgb, keep<MODE>(mul2(neg2(tE), mul2(qq, finv)), m));
+            kahan_add(p.ec, p.kc, keep<MODE>(mul2(qc, rinv), m));
+            if (FLAGS & EF_REP) kahan_add(p.er, p.kr, keep<MODE>(er, m));
         }
     }
     static __device__ __forceinline__ void rotate_data(JState& j, int src) {
@@ -411,9 +443,9 @@ struct Energy {
             sa[288 + lane] += fix(p.phi.y);
         }
         if (FLAGS & EF_ENERGY) {
-            i.egb += fix(p.egb.x) + fix(p.egb.y);
-            i.ec += fix(p.ec.x) + fix(p.ec.y);
-            if (FLAGS & EF_REP) i.er += fix(p.er.x) + fix(p.er.y);
+            i.egb += (fix(p.egb.x) + fix(p.egb.y)) - (fix(p.kgb.x) + fix(p.kgb.y));
+            i.ec += (fix(p.ec.x) + fix(p.ec.y)) - (fix(p.kc.x) + fix(p.kc.y));
+            if (FLAGS & EF_REP) i.er += (fix(p.er.x) + fix(p.er.y)) - (fix(p.kr.x) + fix(p.kr.y));
         }
     }
     template <int FLAGS>
