@@ -632,14 +632,17 @@ struct EnergyF : Energy {
 };
 
 // --- the warp walker ------------------------------------------------------------
-// 32 steps of one (super-row, tile) block: after 32 rotations every j value is
+// The steps of one (super-row, tile) block: after 32 rotations every j value is
 // back in its home lane.
 template <class P, int FLAGS, int MODE, bool FAR>
 __device__ __forceinline__ void run_tile(const PairArgs& A, const typename P::IState& is, typename P::JState& js,
                                          typename P::Part& ip, const BlockInfo& bi, int i0, int jbase, int lane,
                                          int next) {
+    // a DX block pairs the x half with its own tile: only steps 1 .. 16 carry
+    // pairs (js enters rotated by one and leaves rotated by 17)
+    constexpr int K0 = (MODE == M_DX) ? 1 : 0, K1 = (MODE == M_DX) ? 17 : 32;
 #pragma unroll P::UNROLL
-    for (int k = 0; k < 32; ++k) {
+    for (int k = K0; k < K1; ++k) {
         // the next step's j data are fetched before this step's arithmetic, so
         // that only the short accumulator chain is serial between steps
         typename P::JState nx = js;
@@ -710,8 +713,9 @@ __device__ __forceinline__ void walk_task(const PairArgs& A, const int4 t, long 
     P::load_i(A, base, n, 64 * K, lane, is);
     const int next = (lane + 1) & 31;
     for (int c = 0; c < cnt; ++c) {
+        const bool dx = (J == 2 * K);          // see run_tile: entry / exit rotation of a DX block
         typename P::JState js;
-        P::load_j(A, base, n, 32 * J + lane, js);
+        P::load_j(A, base, n, 32 * J + ((lane + (dx ? 1 : 0)) & 31), js);
         typename P::Part ip;
         ip.zero();
         const BlockInfo bi = block_info(A, r, K, J, nb);
@@ -724,7 +728,7 @@ __device__ __forceinline__ void walk_task(const PairArgs& A, const int4 t, long 
             run_tile<P, FLAGS, M_DY, false>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
         }
         P::fold_i(is, sa, lane, ip);
-        P::flush_j(A, base, n, 32 * J + lane, js);
+        P::flush_j(A, base, n, 32 * J + ((lane + (dx ? 17 : 0)) & 31), js);
         if (c + 1 < cnt && ++J == nb) {
             P::flush_i(A, r, base, n, 64 * K, lane, is, sa);
 #pragma unroll
