@@ -29,17 +29,18 @@ LN10 = 2.302585092994045684
 class Params(C.Structure):
     _fields_ = [(k, C.c_double) for k in (
         "alpha", "beta", "gamma", "offset", "eps_in", "eps_out",
-        "bond_k", "bond_r0", "rep_k", "rep_sigma", "dt", "friction", "mass", "kT", "kappa")]
+        "bond_k", "bond_r0", "rep_k", "rep_sigma", "dt", "friction", "mass", "kT", "kappa",
+        "rgbmax", "cut")]
 
 
 def default_params(**kw) -> Params:
     """OBC parameters alpha, beta, gamma = 1.0, 0.8, 4.85, offset 0.09 A,
-    eps_in 1, eps_out 78.5, no salt (kappa = 0); MD driver constants (bond k
-    300 about 1.5 A, soft repulsion k 10 below 2.5 A, 2 fs, 10 / ps, 12 amu,
-    300 K)."""
+    eps_in 1, eps_out 78.5, no salt (kappa = 0), no cutoffs (rgbmax = cut = 0);
+    MD driver constants (bond k 300 about 1.5 A, soft repulsion k 10 below
+    2.5 A, 2 fs, 10 / ps, 12 amu, 300 K)."""
     d = dict(alpha=1.0, beta=0.8, gamma=4.85, offset=0.09, eps_in=1.0, eps_out=78.5,
              bond_k=300.0, bond_r0=1.5, rep_k=10.0, rep_sigma=2.5, dt=0.002, friction=10.0,
-             mass=12.0, kT=KB * 300.0, kappa=0.0)
+             mass=12.0, kT=KB * 300.0, kappa=0.0, rgbmax=0.0, cut=0.0)
     d.update(kw)
     return Params(**d)
 
@@ -63,6 +64,10 @@ def lib():
         _lib.gbo_hct_pair.argtypes = [d, d, d]
         _lib.gbo_hct_pair_dr.restype = d
         _lib.gbo_hct_pair_dr.argtypes = [d, d, d]
+        _lib.gbo_hct_pair_cut.restype = d
+        _lib.gbo_hct_pair_cut.argtypes = [d, d, d, d]
+        _lib.gbo_hct_pair_dr_cut.restype = d
+        _lib.gbo_hct_pair_dr_cut.argtypes = [d, d, d, d]
         _lib.gbo_philox4x64.argtypes = [P, P, P]
         _lib.gbo_born_radii.argtypes = [i64, P, P, P, C.POINTER(Params), P, P, P, P]
         _lib.gbo_born_radii_subset.argtypes = [i64, P, P, P, C.POINTER(Params), P, i64, P]
@@ -90,6 +95,14 @@ def _d(a) -> np.ndarray:
 
 def hct_pair(r: float, a: float, s: float) -> float:
     return lib().gbo_hct_pair(r, a, s)
+
+
+def hct_pair_cut(r: float, a: float, s: float, rc: float) -> float:
+    return lib().gbo_hct_pair_cut(float(r), float(a), float(s), float(rc))
+
+
+def hct_pair_dr_cut(r: float, a: float, s: float, rc: float) -> float:
+    return lib().gbo_hct_pair_dr_cut(float(r), float(a), float(s), float(rc))
 
 
 def hct_pair_dr(r: float, a: float, s: float) -> float:

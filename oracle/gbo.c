@@ -21,6 +21,11 @@
  *     Sec. III.B; pH exchange by analogy with Eq. 12 for protons.
  *   - Philox4x64-10 counter-based generator (Salmon, Moraes, Dror, Shaw,
  *     SC'11), from its published definition.
+ *   - Optional cutoffs (the paper's GB runs use none; its explicit-solvent
+ *     runs use an 8 A direct-space cutoff, Sec. III.D): a Born-radius cutoff
+ *     that restricts the HCT integral to a ball of radius rgbmax about the
+ *     descreened atom, and truncation of the GB and Coulomb pair sums at
+ *     distance `cut`.  Both default to 0 = off.
  *   - BAOAB Langevin splitting (Leimkuhler and Matthews, 2013) for the MD
  *     driver; the paper only says "Langevin dynamics" (Sec. III.D).
  *
@@ -48,6 +53,8 @@ typedef struct {
     double rep_k, rep_sigma;        /* E = k (sigma - r)^2, r < sigma, |i-j|>1 */
     double dt, friction, mass, kT;  /* Langevin driver */
     double kappa;                   /* inverse Debye length of the salt (1/A); 0 = no salt */
+    double rgbmax;                  /* Born-radius cutoff (A); 0 = none */
+    double cut;                     /* pair cutoff of E_GB and E_Coul (A); 0 = none */
 } gbo_params;
 
 /* ------------------------------------------------------------------------ */
@@ -131,6 +138,47 @@ double gbo_hct_pair_dr(double r, double a, double s) {
     return 0.5 * db;
 }
 
+/* The same integral restricted to the ball |y - x_i| < rc (a Born-radius
+ * cutoff: only the part of sphere j within rc of atom i descreens it); rc <= 0
+ * means no cutoff.  Written from the shell integral
+ *   H = int_L^U' f(t) / t^2 dt + int_a^{min(L, rc)} dt / t^2   (engulfed only),
+ * f(t) = (s^2 - (r - t)^2) / (4 r t) the fraction of the shell of radius t
+ * about x_i inside sphere j, U' = min(r + s, rc), whose antiderivative is
+ *   F(t) = -(s^2 - r^2) / (8 r t^2) - 1 / (2 t) - ln(t) / (4 r). */
+static double hct_F(double t, double r, double s) {
+    return -(s * s - r * r) / (8.0 * r * t * t) - 0.5 / t - log(t) / (4.0 * r);
+}
+double gbo_hct_pair_cut(double r, double a, double s, double rc) {
+    if (!(rc > 0.0)) return gbo_hct_pair(r, a, s);
+    if (a >= r + s) return 0.0;
+    double L = fmax(a, fabs(r - s));
+    double Up = fmin(r + s, rc);
+    double H = (Up > L) ? hct_F(Up, r, s) - hct_F(L, r, s) : 0.0;
+    if (a < s - r && a < rc) H += 1.0 / a - 1.0 / fmin(L, rc);
+    return H;
+}
+
+/* dH/dr of gbo_hct_pair_cut: with dF/dt = f(t)/t^2 and
+ * dF/dr = (r^2 + s^2) / (8 r^2 t^2) + ln(t) / (4 r^2) at fixed t. */
+double gbo_hct_pair_dr_cut(double r, double a, double s, double rc) {
+    if (!(rc > 0.0)) return gbo_hct_pair_dr(r, a, s);
+    if (a >= r + s) return 0.0;
+    double L, dL;
+    if (a > fabs(r - s)) { L = a; dL = 0.0; }
+    else { L = fabs(r - s); dL = (r > s) ? 1.0 : -1.0; }
+    double U = r + s, Up = fmin(U, rc), dUp = (U < rc) ? 1.0 : 0.0;
+    double d = 0.0;
+    if (Up > L) {
+        double fU = (s * s - (r - Up) * (r - Up)) / (4.0 * r * Up * Up * Up);
+        double fL = (s * s - (r - L) * (r - L)) / (4.0 * r * L * L * L);
+        double gU = (r * r + s * s) / (8.0 * r * r * Up * Up) + log(Up) / (4.0 * r * r);
+        double gL = (r * r + s * s) / (8.0 * r * r * L * L) + log(L) / (4.0 * r * r);
+        d = (fU * dUp + gU) - (fL * dL + gL);
+    }
+    if (a < s - r && a < rc && L < rc) d += dL / (L * L);
+    return d;
+}
+
 static double dist(const double* x, int64_t i, int64_t j, double d[3]) {
     d[0] = x[3 * j] - x[3 * i];
     d[1] = x[3 * j + 1] - x[3 * i + 1];
@@ -141,7 +189,8 @@ static double dist(const double* x, int64_t i, int64_t j, double d[3]) {
 /* Effective Born radii of one molecule of n atoms.
  *   a_i   = rho_i - offset
  *   s_j   = screen_j * a_j
- *   I_i   = sum_{j != i} H(r_ij; a_i, s_j)
+ *   I_i   = sum_{j != i} H(r_ij; a_i, s_j)   (H restricted to the ball of
+ *           radius rgbmax about x_i when rgbmax > 0, gbo_hct_pair_cut)
  *   psi_i = a_i I_i
  *   R_i   = 1 / (1/a_i - tanh(alpha psi - beta psi^2 + gamma psi^3) / rho_i)
  *   dR_i/dpsi_i = R_i^2 (1 - tanh^2) (alpha - 2 beta psi + 3 gamma psi^2) / rho_i
@@ -155,7 +204,7 @@ static double born_integral(int64_t n, const double* x, const double* rho, const
         double d[3];
         double r = dist(x, i, j, d);
         double s_j = screen[j] * (rho[j] - p->offset);
-        I += gbo_hct_pair(r, a_i, s_j);
+        I += gbo_hct_pair_cut(r, a_i, s_j, p->rgbmax);
     }
     return I;
 }
@@ -215,7 +264,8 @@ static double gb_dg(double f, const gbo_params* p) {
  *   E_GB   = -1/2 k_e sum_i sum_j q_i q_j g(f_ij)   (f_ii = R_i; g above: 
  *            (1/eps_in - 1/eps_out) / f without salt)
  *   E_Coul = (k_e / eps_in) sum_{i<j} q_i q_j / r_ij
- * E[0] = E_GB, E[1] = E_Coul. */
+ * pairs with r_ij > cut are left out when cut > 0 (truncation); self terms
+ * are kept.  E[0] = E_GB, E[1] = E_Coul. */
 void gbo_energy_fixed_radii(int64_t n, const double* x, const double* q, const double* R,
                             const gbo_params* p, double E[2]) {
     double egb = 0.0, ecoul = 0.0;
@@ -227,6 +277,7 @@ void gbo_energy_fixed_radii(int64_t n, const double* x, const double* q, const d
             }
             double d[3];
             double r = dist(x, i, j, d);
+            if (p->cut > 0.0 && r > p->cut) continue;      /* pair cutoff: truncated */
             egb += -0.5 * GBO_KE * q[i] * q[j] * gb_g(f_gb(r, R[i], R[j]), p);
             if (j > i) ecoul += (GBO_KE / p->eps_in) * q[i] * q[j] / r;
         }
@@ -259,6 +310,7 @@ void gbo_energy_forces(int64_t n, const double* x, const double* q, const double
             if (j == i) continue;
             double d[3];
             double r = dist(x, i, j, d);
+            if (p->cut > 0.0 && r > p->cut) continue;      /* pair cutoff: truncated */
             double RR = R[i] * R[j];
             double D = r * r / (4.0 * RR);
             double e = exp(-D);
@@ -295,7 +347,7 @@ void gbo_energy_forces(int64_t n, const double* x, const double* q, const double
                 double d[3];
                 double r = dist(x, i, j, d);
                 double s_j = screen[j] * (rho[j] - p->offset);
-                double dEdr = ci * gbo_hct_pair_dr(r, a_i, s_j);
+                double dEdr = ci * gbo_hct_pair_dr_cut(r, a_i, s_j, p->rgbmax);
                 for (int k = 0; k < 3; ++k) {
                     F[3 * j + k] -= dEdr * d[k] / r;
                     F[3 * i + k] += dEdr * d[k] / r;
