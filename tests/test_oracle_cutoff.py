@@ -88,13 +88,24 @@ def test_large_cutoffs_change_nothing(orc, mol):
     assert np.allclose(o1["F"], o0["F"], rtol=1e-9, atol=1e-10)
 
 
+def cut_in_gap(x, near):
+    """A cutoff near `near` in the middle of the widest gap between pair
+    distances there, so that single- and double-precision comparisons of
+    every pair with it agree."""
+    d = np.linalg.norm(x[:, None] - x[None], axis=2)[np.triu_indices(len(x), 1)]
+    d = np.sort(d[np.abs(d - near) < 0.2])
+    k = int(np.argmax(np.diff(d)))
+    assert d[k + 1] - d[k] > 1e-3
+    return float(np.float32(0.5 * (d[k] + d[k + 1])))
+
+
 def test_pair_cutoff_drops_exactly_the_far_pairs(orc, mol):
     """E(cut) = E(no cut) - sum over pairs with r > cut of the pair's GB and
     Coulomb terms at the same Born radii (each pair's terms from a two-atom
     evaluation minus the two self terms)."""
     x, q, rho, scr = mol
     R = orc.born_radii(x, rho, scr)["R"]
-    cut = 9.0
+    cut = cut_in_gap(x, 9.0)
     E_all = orc.energy_fixed_radii(x, q, R).sum()
     E_cut = orc.energy_fixed_radii(x, q, R, orc.default_params(cut=cut)).sum()
     far = 0.0
@@ -109,9 +120,30 @@ def test_pair_cutoff_drops_exactly_the_far_pairs(orc, mol):
     assert E_cut == pytest.approx(E_all - far, rel=1e-11, abs=1e-9)
 
 
+def test_pair_cutoff_decision_is_single_precision(orc):
+    """Two atoms straddling the cutoff by less than an FP32 ulp of r^2: the
+    pair counts exactly when its float32 r^2 is within the float32 cut^2."""
+    cut = 10.0
+    for dx in (10.0, 10.0 + 1e-7, 10.0 + 4e-7, 10.0 + 6e-7, 10.0 - 4e-7,
+               np.nextafter(np.float32(10.0), np.float32(11.0)),
+               np.nextafter(np.float32(10.0), np.float32(9.0))):
+        x = np.array([[0.0, 0.0, 0.0], [float(dx), 0.0, 0.0]])
+        q = np.array([0.5, -0.5])
+        R = np.array([1.5, 1.5])
+        E = orc.energy_fixed_radii(x, q, R, orc.default_params(cut=cut))
+        r2 = np.float32(dx) * np.float32(dx)
+        inside = r2 <= np.float32(np.float32(cut) * np.float32(cut))
+        assert (E[1] != 0.0) == bool(inside), dx
+    # 10 + 1e-7 is beyond the cutoff in double precision but rounds to 10 in
+    # float: counted
+    x = np.array([[0.0, 0.0, 0.0], [10.0 + 1e-7, 0.0, 0.0]])
+    assert orc.energy_fixed_radii(x, np.array([0.5, -0.5]), np.array([1.5, 1.5]),
+                                  orc.default_params(cut=cut))[1] != 0.0
+
+
 def test_forces_fd_with_both_cutoffs(orc, mol):
     x, q, rho, scr = mol
-    p = orc.default_params(rgbmax=8.0, cut=10.0)
+    p = orc.default_params(rgbmax=8.0, cut=cut_in_gap(x, 10.0))
     o = orc.energy_forces(x, q, rho, scr, p)
     d = np.linalg.norm(x[:, None] - x[None], axis=2)
     rng = np.random.default_rng(4)
@@ -119,7 +151,7 @@ def test_forces_fd_with_both_cutoffs(orc, mol):
     checked = 0
     for _ in range(40):
         i, k = int(rng.integers(len(q))), int(rng.integers(3))
-        if np.any(np.abs(d[i] - 10.0) < 1e-3):     # the truncated energy jumps at r = cut
+        if np.any(np.abs(d[i] - p.cut) < 1e-3):     # the truncated energy jumps at r = cut
             continue
         xp, xm = x.copy(), x.copy()
         xp[i, k] += h
