@@ -52,20 +52,32 @@ typedef struct gb_ctx gb_ctx;
  * Onufriev, Bashford and Case ("igb=2", Sec. III.D) for MD and for every
  * state-change energy; alpha, beta, gamma rescale the HCT integral into the
  * effective Born radius, `offset` is subtracted from each intrinsic radius,
- * eps_in / eps_out are the solute and solvent dielectric constants (no
- * cutoff).  rep_k, rep_sigma: optional soft repulsion
- * rep_k (rep_sigma - r)^2 for r < rep_sigma between atoms more than one
- * position apart in the chain (0 disables it; MD driver only).  kappa: inverse
+ * eps_in / eps_out are the solute and solvent dielectric constants.
+ * rep_k, rep_sigma: optional soft repulsion rep_k (rep_sigma - r)^2 for
+ * r < rep_sigma between atoms more than one position apart in the chain (0
+ * disables it; MD driver only; never cut).  kappa: inverse
  * Debye length of dissolved salt (1/A; 0 = no salt, the paper's setting);
  * the solvent term of every GB pair (and self) term is screened,
  *   (1/eps_in - 1/eps_out) / f  ->  (1/eps_in - exp(-kappa f)/eps_out) / f,
- * in energies, forces, dE/dq and the Monte Carlo energy changes. */
+ * in energies, forces, dE/dq and the Monte Carlo energy changes.
+ * Optional cutoffs (0 = none, the paper's GB setting; both in A, finite):
+ *   rgbmax  Born-radius cutoff: the HCT descreening integral of atom i counts
+ *           only the part of each sphere j that lies within rgbmax of atom i
+ *           (an integral restricted to that ball, so radii stay continuous
+ *           in the coordinates);
+ *   cut     pair cutoff: GB and Coulomb pair terms of pairs farther apart
+ *           than `cut` are left out (truncation; self terms stay) in
+ *           energies, forces, dE/dq and the Monte Carlo energy changes.
+ * With a cutoff the pair kernels skip, per 64 x 32-atom block, every block
+ * whose atoms' bounding boxes prove all its pairs out of range (a block
+ * neighbour list rebuilt from the coordinates of each evaluation). */
 typedef struct {
     float alpha, beta, gamma;
     float offset;
     float eps_in, eps_out;
     float rep_k, rep_sigma;
     float kappa;
+    float rgbmax, cut;
 } gb_params;
 
 /* Create a context for a fixed batch layout.
@@ -294,7 +306,9 @@ int gb_md_segment(gb_ctx* ctx, gb_md_state* state, const gb_sites* sites, int64_
  *
  * Same inputs, outputs and arithmetic as gb_energy_forces for a batch of one
  * replica of n_atoms atoms (1 <= n_atoms <= GB_STATIC_MAX_ATOMS); E_out is
- * double[3].  Works on the current device.  It allocates nothing: no
+ * double[3]; the cutoffs of gb_params apply pair by pair (no block is
+ * skipped: this path builds no bounding boxes).  Works on the current
+ * device.  It allocates nothing: no
  * cudaMalloc, no cudaFree, no allocating library routine.
  *  - The first call on a device looks up the array's device address (once per
  *    device); make that first call before any stream capture.

@@ -45,14 +45,14 @@ class GBError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [(k, C.c_float) for k in
                 ("alpha", "beta", "gamma", "offset", "eps_in", "eps_out", "rep_k", "rep_sigma",
-                 "kappa")]
+                 "kappa", "rgbmax", "cut")]
 
 
 def default_params(**kw) -> Params:
     """OBC alpha, beta, gamma = 1.0, 0.8, 4.85; offset 0.09 A; eps 1 / 78.5;
-    soft repulsion off; no salt (kappa = 0)."""
+    soft repulsion off; no salt (kappa = 0); no cutoffs (rgbmax = cut = 0)."""
     d = dict(alpha=1.0, beta=0.8, gamma=4.85, offset=0.09, eps_in=1.0, eps_out=78.5,
-             rep_k=0.0, rep_sigma=0.0, kappa=0.0)
+             rep_k=0.0, rep_sigma=0.0, kappa=0.0, rgbmax=0.0, cut=0.0)
     d.update(kw)
     return Params(**d)
 

@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libgbremd.so")
-SOURCES = ("api.cu", "pairs.cu", "atoms.cu", "noalloc.cu", "persist.cu")
+SOURCES = ("api.cu", "pairs.cu", "pairs_cut.cu", "atoms.cu", "noalloc.cu", "persist.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

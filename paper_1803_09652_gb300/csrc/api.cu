@@ -234,6 +234,7 @@ gbk::PairArgs pair_args(const gb_ctx* c, const float* xyzq, const float* rad) {
     a.kappa = c->p.kappa;
     a.rep_k = c->p.rep_k;
     a.rep_sigma = c->p.rep_sigma;
+    gbk::set_cutoffs(a, c->p);
     a.I_acc = c->I_acc;
     a.dR_acc = c->dR_acc;
     a.phi_acc = c->phi_acc;
@@ -288,16 +289,17 @@ int evaluate(gb_ctx* c, const float* xyzq, const float* rad, float* R_out, int f
     const gbk::AtomArgs aa = atom_args(c, xyzq, rad);
     if (build_boxes) GB_CHECK(c, gbk::launch_tile_boxes(pa, c->M, c->n_tiles32, s));
     if (ev) GB_CHECK(c, mark(c, ev[0], s));
-    GB_CHECK(c, gbk::launch_pairs(gbk::PASS_BORN, 0, pa, c->tasks, c->wpb, s));
+    GB_CHECK(c, gbk::launch_pairs(gbk::PASS_BORN, gbk::cut_flag(gbk::PASS_BORN, c->p), pa, c->tasks, c->wpb, s));
     if (ev) GB_CHECK(c, mark(c, ev[1], s));
     GB_CHECK(c, gbk::launch_born_finalize(aa, R_out, s));
     if (ev) GB_CHECK(c, mark(c, ev[2], s));
-    GB_CHECK(c, gbk::launch_pairs(gbk::PASS_ENERGY, flags, pa, c->tasks, c->wpb, s));
+    GB_CHECK(c, gbk::launch_pairs(gbk::PASS_ENERGY, flags | gbk::cut_flag(gbk::PASS_ENERGY, c->p), pa, c->tasks,
+                                  c->wpb, s));
     if (ev) GB_CHECK(c, mark(c, ev[3], s));
     GB_CHECK(c, gbk::launch_energy_finalize(aa, (flags & gbk::EF_ENERGY) ? 1 : 0, phi_out, s,
                                             md ? md->bond_k : 0.0f, md ? md->bond_r0 : 0.0f));
     if (ev) GB_CHECK(c, mark(c, ev[4], s));
-    GB_CHECK(c, gbk::launch_pairs(gbk::PASS_CHAIN, 0, pa, c->tasks, c->wpb, s));
+    GB_CHECK(c, gbk::launch_pairs(gbk::PASS_CHAIN, gbk::cut_flag(gbk::PASS_CHAIN, c->p), pa, c->tasks, c->wpb, s));
     if (ev) GB_CHECK(c, mark(c, ev[5], s));
     return GB_OK;
 }
@@ -337,10 +339,7 @@ extern "C" int gb_ctx_create(gb_ctx** out, int32_t n_rep, const int64_t* atom_of
     for (int r = 0; r < n_rep; ++r)
         if (atom_off[r + 1] < atom_off[r]) return fail(nullptr, GB_ERR_INVALID_ARG, "atom_off must be non-decreasing");
     if (atom_off[n_rep] >= (1LL << 31)) return fail(nullptr, GB_ERR_INVALID_ARG, "too many atoms");
-    if (!(params->offset >= 0.0f) || !(params->eps_in > 0.0f) || !(params->eps_out > 0.0f) ||
-        !(params->rep_k >= 0.0f) || !(params->rep_sigma >= 0.0f) || !(params->kappa >= 0.0f) ||
-        !(params->kappa < 1.0e3f))
-        return fail(nullptr, GB_ERR_INVALID_ARG, "invalid GB parameters");
+    if (!gbk::params_ok(*params)) return fail(nullptr, GB_ERR_INVALID_ARG, "invalid GB parameters");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
         return fail(nullptr, GB_ERR_CUDA, "no such CUDA device");
@@ -510,7 +509,7 @@ extern "C" int gb_born_radii(gb_ctx* c, const float* xyzq, const float* rad, flo
     const gbk::PairArgs pa = pair_args(c, xyzq, rad);
     const gbk::AtomArgs aa = atom_args(c, xyzq, rad);
     GB_CHECK(c, gbk::launch_tile_boxes(pa, c->M, c->n_tiles32, s));
-    GB_CHECK(c, gbk::launch_pairs(gbk::PASS_BORN, 0, pa, c->tasks, c->wpb, s));
+    GB_CHECK(c, gbk::launch_pairs(gbk::PASS_BORN, gbk::cut_flag(gbk::PASS_BORN, c->p), pa, c->tasks, c->wpb, s));
     GB_CHECK(c, gbk::launch_born_finalize(aa, R_out, s));
     return GB_OK;
 }
@@ -559,6 +558,7 @@ static gbk::MCArgs mc_args(const gb_ctx* c, const gb_sites* sites, float* xyzq, 
     a.kc = gbk::KE / c->p.eps_in;
     a.ke_out = gbk::KE / c->p.eps_out;
     a.kappa = c->p.kappa;
+    a.cut2 = c->p.cut * c->p.cut;
     a.seed = seed;
     a.step = step;
     a.ctr = nullptr;
@@ -726,6 +726,7 @@ int enqueue_mc(gb_ctx* c, gb_md_state* st, const gb_sites* sites, int64_t k, cud
         a.kc = gbk::KE / c->p.eps_in;
         a.ke_out = gbk::KE / c->p.eps_out;
         a.kappa = c->p.kappa;
+        a.cut2 = c->p.cut * c->p.cut;
         a.seed = st->seed;
         a.step = (u64)k;
         a.ctr = c->ctr;
@@ -786,7 +787,7 @@ int enqueue_steps(gb_ctx* c, gb_md_state* st, const gb_sites* sites, int64_t len
     const int flags = (c->p.rep_k != 0.0f) ? gbk::EF_REP : 0;
     auto mc_due = [&](int64_t t) { return sites && st->mc_every > 0 && t % st->mc_every == 0; };
     auto ex_due = [&](int64_t t) { return sites && st->grid && st->ex_every > 0 && t % st->ex_every == 0; };
-    if (c->use_persist && c->persist_grid > 0 && c->p.kappa == 0.0f) {
+    if (c->use_persist && c->persist_grid > 0 && c->p.kappa == 0.0f && c->p.rgbmax == 0.0f && c->p.cut == 0.0f) {
         gbk::PersistArgs a{};
         a.pa = pair_args(c, xyzq, rad);
         a.aa = aa;

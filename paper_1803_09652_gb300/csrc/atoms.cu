@@ -215,11 +215,13 @@ __device__ __forceinline__ float2 mc_Rh(const MCArgs& A, int64_t g) {
     return A.Rh[g];
 }
 
-// A_kj = k_c / r - tE(f) / f, tE the (screened) solvent factor of gb_screen.
+// A_kj = k_c / r - tE(f) / f, tE the (screened) solvent factor of gb_screen;
+// 0 beyond the pair cutoff (cut2 = cut^2 > 0), as in the energy pass.
 __device__ __forceinline__ float mc_pair_term(float4 xk, float2 Rk, float4 xj, float2 Rj, float tke, float kc,
-                                              float ke_out, float kappa) {
+                                              float ke_out, float kappa, float cut2) {
     const float dx = xj.x - xk.x, dy = xj.y - xk.y, dz = xj.z - xk.z;
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    if (cut2 > 0.0f && r2 > cut2) return 0.0f;
     const float e = __expf(-r2 * (Rk.y * Rj.y));          // exp(-r^2 / (4 R_k R_j))
     const float f2 = fmaf(Rk.x * Rj.x, e, r2);
     const float finv = rsqrtf(f2);
@@ -258,7 +260,7 @@ __global__ void __launch_bounds__(256) k_mc_rows(MCArgs A) {
         for (int j = j0 + lane; j < j1; j += 32) {
             const int64_t gj = base + j;
             const float4 xj = A.xyzq[gj];
-            const float term = (j == lk) ? mc_self_term(Rk.x, tke, kc, keo, kap) : mc_pair_term(xk, Rk, xj, mc_Rh(A, gj), tke, kc, keo, kap);
+            const float term = (j == lk) ? mc_self_term(Rk.x, tke, kc, keo, kap) : mc_pair_term(xk, Rk, xj, mc_Rh(A, gj), tke, kc, keo, kap, A.cut2);
             acc += (double)(xj.w * term);
         }
 #pragma unroll
@@ -313,7 +315,7 @@ __global__ void __launch_bounds__(256) k_mc_decide(MCArgs A) {
             part += s_dq[k] * s_phi[k];
         } else {
             const int64_t gl = base + A.site_atom_idx[a0 + l];
-            Akl = mc_pair_term(A.xyzq[gk], Rk, A.xyzq[gl], mc_Rh(A, gl), tke, kc, keo, kap);
+            Akl = mc_pair_term(A.xyzq[gk], Rk, A.xyzq[gl], mc_Rh(A, gl), tke, kc, keo, kap, A.cut2);
         }
         part += 0.5 * s_dq[k] * s_dq[l] * (double)Akl;
     }
@@ -412,7 +414,7 @@ __global__ void __launch_bounds__(256) k_sweep_rows(MCArgs A) {
         for (int j = j0 + lane; j < j1; j += 32) {
             const int64_t gj = base + j;
             const float4 xj = A.xyzq[gj];
-            const float term = (j == lk) ? mc_self_term(Rk.x, tke, kc, keo, kap) : mc_pair_term(xk, Rk, xj, mc_Rh(A, gj), tke, kc, keo, kap);
+            const float term = (j == lk) ? mc_self_term(Rk.x, tke, kc, keo, kap) : mc_pair_term(xk, Rk, xj, mc_Rh(A, gj), tke, kc, keo, kap, A.cut2);
             acc += (double)(xj.w * term);
         }
 #pragma unroll
@@ -484,7 +486,7 @@ __global__ void __launch_bounds__(256) k_sweep_decide(MCArgs A) {
                 part += s_dq[k] * s_phi[a0 + k];
             } else {
                 const int64_t gl = base + L.atom[a0 + l];
-                Akl = mc_pair_term(A.xyzq[gk], Rk, A.xyzq[gl], mc_Rh(A, gl), tke, kc, keo, kap);
+                Akl = mc_pair_term(A.xyzq[gk], Rk, A.xyzq[gl], mc_Rh(A, gl), tke, kc, keo, kap, A.cut2);
             }
             part += 0.5 * s_dq[k] * s_dq[l] * (double)Akl;
         }
@@ -510,7 +512,7 @@ __global__ void __launch_bounds__(256) k_sweep_decide(MCArgs A) {
                 double d = 0.0;
                 for (int a = 0; a < na; ++a) {
                     const int64_t ga = base + L.atom[a0 + a];
-                    const float Ama = (ga == gm) ? mc_self_term(Rm.x, tke, kc, keo, kap) : mc_pair_term(xm, Rm, A.xyzq[ga], mc_Rh(A, ga), tke, kc, keo, kap);
+                    const float Ama = (ga == gm) ? mc_self_term(Rm.x, tke, kc, keo, kap) : mc_pair_term(xm, Rm, A.xyzq[ga], mc_Rh(A, ga), tke, kc, keo, kap, A.cut2);
                     d += s_dq[a] * (double)Ama;
                 }
                 s_phi[m] += d;

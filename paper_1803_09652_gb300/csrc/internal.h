@@ -22,6 +22,9 @@ struct PairArgs {
     float ke_out, kappa;       // k_e / eps_out and the salt's inverse Debye length (EF_SALT)
     float kc;                  // k_e / eps_in
     float rep_k, rep_sigma;    // soft repulsion (rep_k == 0: off)
+    float rgbmax;              // Born-radius cutoff (EF_CUT kernels of the Born and chain passes)
+    float cut2;                // pair cutoff squared (EF_CUT kernels of the energy pass)
+    float e_range2;            // energy-pass block range squared: max(cut, rep_sigma)^2
     u64* I_acc;                // [N]   Born integrals, 2^40 fixed point
     u64* dR_acc;               // [N]   dE/dR pair part, 2^32
     u64* phi_acc;              // [N]   dE/dq pair part, 2^32
@@ -45,11 +48,34 @@ struct TaskList {
 
 enum PassKind { PASS_BORN = 0, PASS_ENERGY = 1, PASS_CHAIN = 2 };
 
-// flags for the energy pass
-enum { EF_ENERGY = 1, EF_PHI = 2, EF_REP = 4, EF_SALT = 8 };
+// flags for the energy pass; EF_CUT for any pass: the kernel applies the
+// pass's cutoff (Born and chain passes: rgbmax; energy pass: cut), skipping
+// out-of-range blocks.  EF_STRADDLE is internal to the walker: the block has
+// pairs on both sides of the cutoff and tests each pair.
+enum { EF_ENERGY = 1, EF_PHI = 2, EF_REP = 4, EF_SALT = 8, EF_CUT = 16, EF_STRADDLE = 32 };
 
 cudaError_t launch_pairs(int pass, int flags, const PairArgs& a, const TaskList& t,
                          int warps_per_block, cudaStream_t s);
+// the EF_CUT kernels (pairs_cut.cu); launch_pairs forwards to it
+cudaError_t launch_pairs_cut(int pass, int flags, const PairArgs& a, const TaskList& t,
+                             int warps_per_block, cudaStream_t s);
+
+// Cutoff fields of the pair arguments, and the EF_CUT flag of each pass.
+inline void set_cutoffs(PairArgs& a, const gb_params& p) {
+    a.rgbmax = p.rgbmax;
+    a.cut2 = p.cut * p.cut;
+    const float er = (p.rep_k != 0.0f && p.rep_sigma > p.cut) ? p.rep_sigma : p.cut;
+    a.e_range2 = er * er;
+}
+inline int cut_flag(int pass, const gb_params& p) {
+    return (pass == PASS_ENERGY ? p.cut > 0.0f : p.rgbmax > 0.0f) ? EF_CUT : 0;
+}
+// Parameter checks shared by every entry point that takes gb_params.
+inline bool params_ok(const gb_params& p) {
+    return p.offset >= 0.0f && p.eps_in > 0.0f && p.eps_out > 0.0f && p.rep_k >= 0.0f &&
+           p.rep_sigma >= 0.0f && p.kappa >= 0.0f && p.kappa < 1.0e3f && p.rgbmax >= 0.0f &&
+           p.rgbmax < 1.0e6f && p.cut >= 0.0f && p.cut < 1.0e6f;
+}
 
 // Work units (32-atom tiles against 64-atom super-rows) of an n-atom replica.
 int64_t pair_units(int64_t n);
@@ -134,6 +160,7 @@ struct MCArgs {
     double kT;
     double tau_ke, kc;
     double ke_out, kappa;      // salt screening of the solvent term (kappa 0: none)
+    float cut2;                // pair cutoff squared (0: none)
     u64 seed;
     u64 step;
     const u64* ctr;            // when non-null the step is ctr[0] + step

@@ -97,9 +97,7 @@ extern "C" int gb_energy_forces_static(int32_t n_atoms, const gb_params* params,
     if (!params || !xyzq || !rad_screen) return GB_ERR_INVALID_ARG;
     if (!R_out && !F_fixed && !F_out && !E_out && !dEdq_out) return GB_ERR_INVALID_ARG;
     if (((uintptr_t)xyzq % 16) || ((uintptr_t)rad_screen % 8)) return GB_ERR_INVALID_ARG;
-    if (!(params->eps_in > 0.0f) || !(params->eps_out > 0.0f) || !(params->offset >= 0.0f) ||
-        !(params->kappa >= 0.0f) || !(params->kappa < 1.0e3f))
-        return GB_ERR_INVALID_ARG;
+    if (!gbk::params_ok(*params)) return GB_ERR_INVALID_ARG;
     unsigned char* base = nullptr;
     int rc = scratch_for_current_device(&base);
     if (rc) return rc;
@@ -140,6 +138,7 @@ extern "C" int gb_energy_forces_static(int32_t n_atoms, const gb_params* params,
     pa.kappa = params->kappa;
     pa.rep_k = params->rep_k;
     pa.rep_sigma = params->rep_sigma;
+    gbk::set_cutoffs(pa, *params);
     pa.I_acc = I_acc;
     pa.dR_acc = dR_acc;
     pa.phi_acc = phi_acc;
@@ -178,11 +177,16 @@ extern "C" int gb_energy_forces_static(int32_t n_atoms, const gb_params* params,
     const int flags = (E_out ? gbk::EF_ENERGY : 0) | (dEdq_out ? gbk::EF_PHI : 0) |
                       (params->rep_k != 0.0f ? gbk::EF_REP : 0) | (params->kappa != 0.0f ? gbk::EF_SALT : 0);
     const int wpb = 8;
-    if (gbk::launch_pairs(gbk::PASS_BORN, 0, pa, tl, wpb, s) != cudaSuccess) return GB_ERR_CUDA;
+    const gb_params& P = *params;
+    if (gbk::launch_pairs(gbk::PASS_BORN, gbk::cut_flag(gbk::PASS_BORN, P), pa, tl, wpb, s) != cudaSuccess)
+        return GB_ERR_CUDA;
     if (gbk::launch_born_finalize(aa, R_out, s) != cudaSuccess) return GB_ERR_CUDA;
-    if (gbk::launch_pairs(gbk::PASS_ENERGY, flags, pa, tl, wpb, s) != cudaSuccess) return GB_ERR_CUDA;
+    if (gbk::launch_pairs(gbk::PASS_ENERGY, flags | gbk::cut_flag(gbk::PASS_ENERGY, P), pa, tl, wpb, s) !=
+        cudaSuccess)
+        return GB_ERR_CUDA;
     if (gbk::launch_energy_finalize(aa, E_out ? 1 : 0, dEdq_out, s) != cudaSuccess) return GB_ERR_CUDA;
-    if (gbk::launch_pairs(gbk::PASS_CHAIN, 0, pa, tl, wpb, s) != cudaSuccess) return GB_ERR_CUDA;
+    if (gbk::launch_pairs(gbk::PASS_CHAIN, gbk::cut_flag(gbk::PASS_CHAIN, P), pa, tl, wpb, s) != cudaSuccess)
+        return GB_ERR_CUDA;
     if (gbk::launch_forces_out(aa, F_fixed, F_out, E_out, s) != cudaSuccess) return GB_ERR_CUDA;
     return GB_OK;
 }

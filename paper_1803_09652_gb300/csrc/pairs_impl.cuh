@@ -150,6 +150,135 @@ __device__ __forceinline__ f2 hct_closed_fr2(f2 r, f2 rinv, f2 a, f2 s) {
     return make_float2(a.x >= U.x ? 0.0f : fr.x, a.y >= U.y ? 0.0f : fr.y);
 }
 
+// --- the same integral restricted to the ball |y - x_i| < rc (Born-radius cutoff) ---
+// Shells about x_i now run from L to U' = min(U, rc): the bracket of
+// hct_closed2 with U' in place of U when L < U' (else no shell term), and the
+// engulfed part 2 (1/a - 1/min(L, rc)) when a < s - r and a < rc.  irc = 1/rc.
+// Serves the pairs of blocks that straddle the cutoff, where sphere j reaches
+// past rc (r + s > rc); it is exact (to rounding) for every geometry, so the
+// lanes of such a step that do not reach past rc may take it too.
+__device__ __forceinline__ f2 hct_cut2(f2 r, f2 rinv, f2 a, f2 s, float rc, float irc) {
+    const f2 U = add2(r, s);
+    const f2 Up = make_float2(fminf(U.x, rc), fminf(U.y, rc));
+    const f2 rs = add2(r, neg2(s));
+    const f2 L = make_float2(fmaxf(a.x, fabsf(rs.x)), fmaxf(a.y, fabsf(rs.y)));
+    const f2 iU = rcp2(Up), iL = rcp2(L);
+    const f2 dU2 = add2(mul2(iU, iU), neg2(mul2(iL, iL)));
+    const f2 w = fma2(neg2(mul2(s, s)), rinv, r);
+    f2 b = fma2(mul2(F2(0.25f), w), dU2, add2(iL, neg2(iU)));
+    b = fma2(mul2(F2(0.5f), rinv), logv(mul2(L, iU)), b);
+    b.x = (L.x < Up.x) ? b.x : 0.0f;
+    b.y = (L.y < Up.y) ? b.y : 0.0f;
+    const f2 iLc = make_float2(L.x < rc ? iL.x : irc, L.y < rc ? iL.y : irc);
+    const f2 eng = mul2(F2(2.0f), add2(rcp2(a), neg2(iLc)));
+    b.x += (a.x < -rs.x && a.x < rc) ? eng.x : 0.0f;
+    b.y += (a.y < -rs.y && a.y < rc) ? eng.y : 0.0f;
+    return mul2(F2(0.5f), b);
+}
+
+// -(dH/dr)/r of hct_cut2.  As hct_closed_fr2 with dU = dU'/dr (1 while
+// U < rc, 0 once U' = rc) in the terms that came from the upper limit:
+//   dB/dr = -dL/L^2 + dU/U'^2 + (1 + s^2/r^2)/4 (1/U'^2 - 1/L^2)
+//           + w/2 (dL/L^3 - dU/U'^3) - ln(L/U') / (2 r^2) + (dL/L - dU/U') / (2r)
+// (0 when L >= U'), plus 2 dL/L^2 when engulfed with L < rc.
+__device__ __forceinline__ f2 hct_cut_fr2(f2 r, f2 rinv, f2 a, f2 s, float rc) {
+    const f2 U = add2(r, s);
+    const bool cx = U.x > rc, cy = U.y > rc;
+    const f2 Up = make_float2(cx ? rc : U.x, cy ? rc : U.y);
+    const f2 rs = add2(r, neg2(s));
+    const bool on_x = a.x > fabsf(rs.x), on_y = a.y > fabsf(rs.y);
+    const f2 L = make_float2(on_x ? a.x : fabsf(rs.x), on_y ? a.y : fabsf(rs.y));
+    const f2 dL = make_float2(on_x ? 0.0f : (rs.x > 0.0f ? 1.0f : -1.0f),
+                              on_y ? 0.0f : (rs.y > 0.0f ? 1.0f : -1.0f));
+    const f2 iU = rcp2(Up), iL = rcp2(L);
+    const f2 iUd = make_float2(cx ? 0.0f : iU.x, cy ? 0.0f : iU.y);   // dU / U'
+    const f2 iU2 = mul2(iU, iU), iL2 = mul2(iL, iL);
+    const f2 s2r2 = mul2(mul2(s, s), mul2(rinv, rinv));
+    const f2 w = fma2(neg2(s2r2), r, r);
+    const f2 dLiL = mul2(dL, iL);
+    f2 db = fma2(neg2(dLiL), iL, mul2(iUd, iU));
+    db = fma2(mul2(F2(0.25f), add2(F2(1.0f), s2r2)), add2(iU2, neg2(iL2)), db);
+    db = fma2(mul2(F2(0.5f), w), add2(mul2(dLiL, iL2), neg2(mul2(iUd, iU2))), db);
+    const f2 hr = mul2(F2(0.5f), rinv);
+    db = fma2(neg2(mul2(hr, rinv)), logv(mul2(L, iU)), db);
+    db = fma2(hr, add2(dLiL, neg2(iUd)), db);
+    db.x = (L.x < Up.x) ? db.x : 0.0f;
+    db.y = (L.y < Up.y) ? db.y : 0.0f;
+    db.x += (a.x < -rs.x && a.x < rc && L.x < rc) ? 2.0f * dLiL.x * iL.x : 0.0f;
+    db.y += (a.y < -rs.y && a.y < rc && L.y < rc) ? 2.0f * dLiL.y * iL.y : 0.0f;
+    return mul2(mul2(F2(-0.5f), db), rinv);
+}
+
+// Disjoint spheres (r >= a + s) reaching past rc: the shells run from
+// L = r - s, and with u = t - L, w = min(rc - L, 2s), x = w / L the integral
+// takes a form without cancelling O(1/L) terms,
+//   H = 1/(4r) [ (2s/L) J1(x) - J2(x) ],
+//   J1 = x^2 / (2 (1+x)^2),   J2 = ln(1+x) - x (2 + 3x) / (2 (1+x)^2)
+// (J1 = int_0^x y/(1+y)^3 dy, J2 = int_0^x y^2/(1+y)^3 dy), w = 2s giving the
+// whole sphere.  w is formed as (rc - r) + s: rc - r is exact for the pairs
+// near the cutoff, so w carries one rounding.  Lanes with w <= 0 (sphere j
+// wholly past rc, masked lanes) give 0.
+__device__ __forceinline__ f2 log1pv(f2 x) { return make_float2(log1pf(x.x), log1pf(x.y)); }
+struct CutFar {
+    f2 x, iL, J1, B;
+    bool cx, cy;                      // w = rc - L (the cutoff limits the shells)
+};
+__device__ __forceinline__ CutFar hct_cut_far_terms(f2 r, f2 s, float rc) {
+    CutFar c;
+    const f2 L = add2(r, neg2(s));
+    c.iL = rcp2(L);
+    const f2 wc = add2(add2(F2(rc), neg2(r)), s);
+    const f2 s2 = add2(s, s);
+    c.cx = wc.x < s2.x;
+    c.cy = wc.y < s2.y;
+    const f2 w = make_float2(fmaxf(0.0f, c.cx ? wc.x : s2.x), fmaxf(0.0f, c.cy ? wc.y : s2.y));
+    c.x = mul2(w, c.iL);
+    const f2 i1 = rcp2(add2(F2(1.0f), c.x));
+    const f2 i12 = mul2(i1, i1);
+    c.J1 = mul2(mul2(F2(0.5f), mul2(c.x, c.x)), i12);
+    const f2 J2 = add2(log1pv(c.x), neg2(mul2(mul2(mul2(F2(0.5f), c.x), fma2(F2(3.0f), c.x, F2(2.0f))), i12)));
+    c.B = fma2(mul2(s2, c.iL), c.J1, neg2(J2));
+    return c;
+}
+__device__ __forceinline__ f2 hct_cut_far2(f2 r, f2 rinv, f2 s, float rc) {
+    return mul2(mul2(F2(0.25f), rinv), hct_cut_far_terms(r, s, rc).B);
+}
+// -(dH/dr)/r of hct_cut_far2: with x' = -(1+x)/L while the cutoff limits the
+// shells and -x/L otherwise,
+//   dB/dr = -(2s/L^2) J1 + x' x (2s/L - x) / (1+x)^3,   dH/dr = (dB/dr - B/r) / (4r),
+// where no two terms cancel.
+__device__ __forceinline__ f2 hct_cut_far_fr2(f2 r, f2 rinv, f2 s, float rc) {
+    const CutFar c = hct_cut_far_terms(r, s, rc);
+    const f2 s2 = add2(s, s);
+    const f2 i1 = rcp2(add2(F2(1.0f), c.x));
+    const f2 xp = mul2(neg2(c.iL), make_float2(c.cx ? 1.0f + c.x.x : c.x.x, c.cy ? 1.0f + c.x.y : c.x.y));
+    const f2 t = mul2(mul2(mul2(xp, c.x), fma2(s2, c.iL, neg2(c.x))), mul2(mul2(i1, i1), i1));
+    const f2 dB = fma2(neg2(mul2(s2, mul2(c.iL, c.iL))), c.J1, t);
+    const f2 dH = mul2(mul2(F2(0.25f), rinv), fma2(neg2(c.B), rinv, dB));
+    return mul2(neg2(dH), rinv);
+}
+// One direction (descreened atom radius a, descreening sphere s) of a pair
+// that reaches past rc: the disjoint form where the spheres are apart, the
+// general restricted closed form (vote) where they overlap.
+__device__ __forceinline__ f2 hct_cut_dir2(f2 r, f2 rinv, f2 a, f2 s, float rc) {
+    const bool d0 = r.x >= a.x + s.x, d1 = r.y >= a.y + s.y;
+    f2 h = hct_cut_far2(r, rinv, s, rc);
+    if (__any_sync(0xffffffffu, !(d0 && d1))) {
+        const f2 g = hct_cut2(r, rinv, a, s, rc, 1.0f / rc);
+        h = make_float2(d0 ? h.x : g.x, d1 ? h.y : g.y);
+    }
+    return h;
+}
+__device__ __forceinline__ f2 hct_cut_dir_fr2(f2 r, f2 rinv, f2 a, f2 s, float rc) {
+    const bool d0 = r.x >= a.x + s.x, d1 = r.y >= a.y + s.y;
+    f2 h = hct_cut_far_fr2(r, rinv, s, rc);
+    if (__any_sync(0xffffffffu, !(d0 && d1))) {
+        const f2 g = hct_cut_fr2(r, rinv, a, s, rc);
+        h = make_float2(d0 ? h.x : g.x, d1 ? h.y : g.y);
+    }
+    return h;
+}
+
 __device__ __forceinline__ long long warp_sum_ll(long long v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -168,6 +297,7 @@ enum { M_FULL = 0, M_DX = 1, M_DY = 2 };
 struct BlockInfo {
     bool far;
     float t_near;
+    float skip2;      // EF_STRADDLE blocks: a step whose pairs all have r^2 > skip2 adds nothing
 };
 struct Mask {
     bool x, y;
@@ -191,6 +321,8 @@ __device__ __forceinline__ f2 safe_r2(f2 r2, Mask m) {
     return make_float2(m.x ? r2.x : FAR_R2, m.y ? r2.y : FAR_R2);
 }
 
+__device__ __forceinline__ f2 sel2(f2 v, Mask m) { return make_float2(m.x ? v.x : 0.0f, m.y ? v.y : 0.0f); }
+
 // Lanes past a replica's end hold ghost atoms (see ghost_x): zero charge,
 // zero descreening radius, zero chain factor, parked far away.
 __device__ __forceinline__ void load_xas(const PairArgs& A, int64_t base, int n, int i, float& x,
@@ -210,6 +342,7 @@ __device__ __forceinline__ void load_xas(const PairArgs& A, int64_t base, int n,
 struct Born {
     static constexpr int NQ = 1;      // int64 i-side accumulators per atom (shared memory)
     static constexpr int UNROLL = 1;  // rotation steps unrolled (measured best per pass)
+    static constexpr bool RADIUS_CUT = true;   // EF_CUT: the cutoff is rgbmax
     struct IState {
         f2 nx, ny, nz, a, s, s2, hs3;   // nx = -x
     };
@@ -232,7 +365,7 @@ struct Born {
         st.acc = 0.0f;
     }
     template <int FLAGS, int MODE, bool FAR>
-    static __device__ __forceinline__ void pair(const PairArgs&, const IState& i, JState& j, Part& p, Mask m,
+    static __device__ __forceinline__ void pair(const PairArgs& A, const IState& i, JState& j, Part& p, Mask m,
                                                 const BlockInfo& bi, int, int, int) {
         const f2 dx = add2(F2(j.x), i.nx), dy = add2(F2(j.y), i.ny), dz = add2(F2(j.z), i.nz);
         const f2 r2 = safe_r2<MODE>(fma2(dx, dx, fma2(dy, dy, mul2(dz, dz))), m);
@@ -274,6 +407,20 @@ struct Born {
                 h_ji = make_float2(c0 ? hc.x : h_ji.x, c1 ? hc.y : h_ji.y);
             }
         }
+        if (FLAGS & EF_STRADDLE) {   // directions whose sphere reaches past rgbmax
+            const f2 r = mul2(r2, rinv);
+            const float rc = A.rgbmax;
+            const bool u0 = r.x + j.s > rc, u1 = r.y + j.s > rc;
+            const bool v0 = r.x + i.s.x > rc, v1 = r.y + i.s.y > rc;
+            if (__any_sync(0xffffffffu, u0 || u1)) {
+                const f2 hc = hct_cut_dir2(r, rinv, i.a, F2(j.s), rc);
+                h_ij = make_float2(u0 ? hc.x : h_ij.x, u1 ? hc.y : h_ij.y);
+            }
+            if (__any_sync(0xffffffffu, v0 || v1)) {
+                const f2 hc = hct_cut_dir2(r, rinv, F2(j.a), i.s, rc);
+                h_ji = make_float2(v0 ? hc.x : h_ji.x, v1 ? hc.y : h_ji.y);
+            }
+        }
         h_ij = keep<MODE>(h_ij, m);
         h_ji = keep<MODE>(h_ji, m);
         p.I = add2(p.I, h_ij);
@@ -313,6 +460,7 @@ struct Born {
 struct Energy {
     static constexpr int NQ = 5;      // fx, fy, fz, dE/dR, dE/dq (shared memory)
     static constexpr int UNROLL = 1;
+    static constexpr bool RADIUS_CUT = false;  // EF_CUT: the cutoff is `cut`
     struct IState {
         f2 nx, ny, nz, q, R, nh;
         long long egb, ec, er;
@@ -379,6 +527,13 @@ struct Energy {
         const f2 qc = mul2(qq, F2(A.kc));
         f2 fr = fma2(qc, mul2(rinv2, rinv), mul2(w, nu));
         f2 G = mul2(mul2(w, e), fma2(nDl, F2(-LN2), F2(1.0f)));        // w e (1 + D)
+        Mask cm{true, true};          // pair within the cutoff (EF_STRADDLE blocks test it)
+        if (FLAGS & EF_STRADDLE) {
+            cm.x = r2.x <= A.cut2;
+            cm.y = r2.y <= A.cut2;
+            fr = sel2(fr, cm);
+            G = sel2(G, cm);
+        }
         f2 er = F2(0.0f);
         if ((FLAGS & EF_REP) && !FAR) {
             const float sig2 = A.rep_sigma * A.rep_sigma;
@@ -407,15 +562,21 @@ struct Energy {
         p.dR = fma2(G, F2(j.R), p.dR);
         j.dR = fmaf(G.y, i.R.y, fmaf(G.x, i.R.x, j.dR));
         if (FLAGS & EF_PHI) {
-            const f2 P = keep<MODE>(fma2(neg2(tE), finv, mul2(F2(A.kc), rinv)), m);
+            f2 P = keep<MODE>(fma2(neg2(tE), finv, mul2(F2(A.kc), rinv)), m);
+            if (FLAGS & EF_STRADDLE) P = sel2(P, cm);
             p.phi = fma2(P, F2(j.q), p.phi);
             j.phi = fmaf(P.y, i.q.y, fmaf(P.x, i.q.x, j.phi));
         }
         if (FLAGS & EF_ENERGY) {
             // the pair energies are large terms that cancel: compensated
             // (Kahan) FP32 sums within the block
-            kahan_add(p.egb, p.kgb, keep<MODE>(mul2(neg2(tE), mul2(qq, finv)), m));
-            kahan_add(p.ec, p.kc, keep<MODE>(mul2(qc, rinv), m));
+            f2 eg = keep<MODE>(mul2(neg2(tE), mul2(qq, finv)), m), ecl = keep<MODE>(mul2(qc, rinv), m);
+            if (FLAGS & EF_STRADDLE) {
+                eg = sel2(eg, cm);
+                ecl = sel2(ecl, cm);
+            }
+            kahan_add(p.egb, p.kgb, eg);
+            kahan_add(p.ec, p.kc, ecl);
             if (FLAGS & EF_REP) kahan_add(p.er, p.kr, keep<MODE>(er, m));
         }
     }
@@ -494,6 +655,7 @@ struct Energy {
 struct Chain {
     static constexpr int NQ = 3;      // fx, fy, fz (shared memory)
     static constexpr int UNROLL = 2;
+    static constexpr bool RADIUS_CUT = true;   // EF_CUT: the cutoff is rgbmax
     struct IState {
         f2 nx, ny, nz, a, s, s2, hs3, c;
     };
@@ -521,7 +683,7 @@ struct Chain {
         st.fx = st.fy = st.fz = 0.0f;
     }
     template <int FLAGS, int MODE, bool FAR>
-    static __device__ __forceinline__ void pair(const PairArgs&, const IState& i, JState& j, Part& p, Mask m,
+    static __device__ __forceinline__ void pair(const PairArgs& A, const IState& i, JState& j, Part& p, Mask m,
                                                 const BlockInfo& bi, int, int, int) {
         const f2 dx = add2(F2(j.x), i.nx), dy = add2(F2(j.y), i.ny), dz = add2(F2(j.z), i.nz);
         const f2 r2 = safe_r2<MODE>(fma2(dx, dx, fma2(dy, dy, mul2(dz, dz))), m);
@@ -569,6 +731,16 @@ struct Chain {
             }
             const f2 fbc = add2(fb, fc);
             fr = make_float2(b0 || c0 ? fbc.x : fr.x, b1 || c1 ? fbc.y : fr.y);
+        }
+        if (FLAGS & EF_STRADDLE) {   // a direction reaches past rgbmax: both from the cut form
+            const f2 r = mul2(r2, rinv);
+            const float rc = A.rgbmax;
+            const bool u0 = r.x + j.s > rc || r.x + i.s.x > rc, u1 = r.y + j.s > rc || r.y + i.s.y > rc;
+            if (__any_sync(0xffffffffu, u0 || u1)) {
+                const f2 fbc = fma2(i.c, hct_cut_dir_fr2(r, rinv, i.a, F2(j.s), rc),
+                                    mul2(F2(j.c), hct_cut_dir_fr2(r, rinv, F2(j.a), i.s, rc)));
+                fr = make_float2(u0 ? fbc.x : fr.x, u1 ? fbc.y : fr.y);
+            }
         }
         fr = keep<MODE>(fr, m);
         p.sx = fma2(fr, dx, p.sx); p.sy = fma2(fr, dy, p.sy); p.sz = fma2(fr, dz, p.sz);
@@ -648,7 +820,15 @@ __device__ __forceinline__ void run_tile(const PairArgs& A, const typename P::IS
         typename P::JState nx = js;
         P::rotate_data(nx, next);
         const Mask m = step_mask<MODE>(k, lane);
-        P::template pair<FLAGS, MODE, FAR>(A, is, js, ip, m, bi, i0, jbase, k);
+        bool busy = true;
+        if (FLAGS & EF_STRADDLE) {   // every pair of this step wholly past the cutoff's reach
+            const float dx0 = js.x + is.nx.x, dy0 = js.y + is.ny.x, dz0 = js.z + is.nz.x;
+            const float dx1 = js.x + is.nx.y, dy1 = js.y + is.ny.y, dz1 = js.z + is.nz.y;
+            const float q0 = fmaf(dx0, dx0, fmaf(dy0, dy0, dz0 * dz0));
+            const float q1 = fmaf(dx1, dx1, fmaf(dy1, dy1, dz1 * dz1));
+            busy = __any_sync(0xffffffffu, fminf(q0, q1) <= bi.skip2);
+        }
+        if (busy) P::template pair<FLAGS, MODE, FAR>(A, is, js, ip, m, bi, i0, jbase, k);
         P::rotate_acc(js, next);
         P::take_data(js, nx);
     }
@@ -662,8 +842,10 @@ __device__ __forceinline__ void run_tile(const PairArgs& A, const typename P::IS
 // directions of a pair disjoint with (s/r)^2 <= YMAX (far-field form valid),
 // so only steps with a closer pair need the exact tests.  Without boxes
 // nothing is proven.
+template <class P>
 __device__ __forceinline__ BlockInfo block_info(const PairArgs& A, int r, int K, int J, int nb) {
     BlockInfo bi;
+    bi.skip2 = INFINITY;
     if (!A.boxes) {
         bi.far = false;
         bi.t_near = INFINITY;
@@ -688,7 +870,69 @@ __device__ __forceinline__ BlockInfo block_info(const PairArgs& A, int r, int K,
     // thresholds rounded up a little, so that rounding in r^2 cannot admit a
     // pair the exact test would reject
     bi.t_near = 1.0001f * fmaxf(as * as, smax * smax * (1.0f / GB_POLY_YMAX));
+    // past the cutoff's reach (a pair wholly beyond adds exact zeros): Born and
+    // chain passes r >= rgbmax + s for both spheres, energy pass r > max(cut, rep_sigma)
+    if (P::RADIUS_CUT) {
+        const float reach = A.rgbmax + smax;
+        bi.skip2 = 1.001f * reach * reach;
+    } else {
+        bi.skip2 = 1.001f * A.e_range2;
+    }
     return bi;
+}
+
+// Cutoff window (EF_CUT kernels): lane l classifies block (K, J0 + l) from the
+// tile bounding boxes, and two ballots give the warp the in-range and the
+// straddle bits of 32 consecutive blocks of the super-row at once.  With
+// rmin / rmax the least / greatest distance between the super-row's box and
+// the tile's box and smax the largest screened radius in either:
+//   Born and chain passes (rgbmax): in range when rmin < rgbmax + smax (some
+//     sphere j reaches into the ball about some i), straddling when
+//     rmax + smax > rgbmax (some sphere reaches past it);
+//   energy pass (cut): in range when rmin <= max(cut, rep_sigma), straddling
+//     when rmax > cut.
+// The bounds carry a 0.1 % margin, so that FP32 rounding of a pair's r^2 can
+// never move it across a decision taken for its block.  A block that is not
+// straddling needs no per-pair test; one out of range is skipped.  Without
+// boxes every block is in range and straddling.
+template <class P>
+__device__ __forceinline__ void cut_window(const PairArgs& A, int r, int K, int J0, int nb, int lane,
+                                           unsigned& in_mask, unsigned& st_mask) {
+    if (!A.boxes) {
+        in_mask = st_mask = 0xffffffffu;
+        return;
+    }
+    const int t0 = A.tile_off[r];
+    float4 il = __ldcg(&A.boxes[2 * (t0 + 2 * K)]), ih = __ldcg(&A.boxes[2 * (t0 + 2 * K) + 1]);
+    if (2 * K + 1 < nb) {
+        const float4 l1 = __ldcg(&A.boxes[2 * (t0 + 2 * K + 1)]), h1 = __ldcg(&A.boxes[2 * (t0 + 2 * K + 1) + 1]);
+        il = make_float4(fminf(il.x, l1.x), fminf(il.y, l1.y), fminf(il.z, l1.z), fmaxf(il.w, l1.w));
+        ih = make_float4(fmaxf(ih.x, h1.x), fmaxf(ih.y, h1.y), fmaxf(ih.z, h1.z), fmaxf(ih.w, h1.w));
+    }
+    const int J = J0 + lane;
+    bool in = false, st = false;
+    if (J < nb) {
+        const float4 jl = __ldcg(&A.boxes[2 * (t0 + J)]), jh = __ldcg(&A.boxes[2 * (t0 + J) + 1]);
+        const float gx = fmaxf(0.0f, fmaxf(il.x - jh.x, jl.x - ih.x));
+        const float gy = fmaxf(0.0f, fmaxf(il.y - jh.y, jl.y - ih.y));
+        const float gz = fmaxf(0.0f, fmaxf(il.z - jh.z, jl.z - ih.z));
+        const float mx = fmaxf(ih.x - jl.x, jh.x - il.x);
+        const float my = fmaxf(ih.y - jl.y, jh.y - il.y);
+        const float mz = fmaxf(ih.z - jl.z, jh.z - il.z);
+        const float rmin2 = gx * gx + gy * gy + gz * gz;
+        const float rmax2 = mx * mx + my * my + mz * mz;
+        if (P::RADIUS_CUT) {
+            const float smax = fmaxf(ih.w, jh.w);
+            const float reach = A.rgbmax + smax, inner = A.rgbmax - smax;
+            in = rmin2 <= 1.001f * reach * reach;
+            st = inner <= 0.0f || rmax2 >= 0.999f * inner * inner;
+        } else {
+            in = rmin2 <= 1.001f * A.e_range2;
+            st = rmax2 >= 0.999f * A.cut2;
+        }
+    }
+    in_mask = __ballot_sync(0xffffffffu, in);
+    st_mask = __ballot_sync(0xffffffffu, st);
 }
 
 // Work of replica r is walked as super-rows K = 0 .. ceil(nb/2) - 1 (nb tiles
@@ -712,25 +956,47 @@ __device__ __forceinline__ void walk_task(const PairArgs& A, const int4 t, long 
     typename P::IState is;
     P::load_i(A, base, n, 64 * K, lane, is);
     const int next = (lane + 1) & 31;
+    // EF_CUT: straddling blocks run the pair code with EF_STRADDLE
+    constexpr int FS = (FLAGS & EF_CUT) ? (FLAGS | EF_STRADDLE) : FLAGS;
+    unsigned w_in = 0xffffffffu, w_st = 0u;
+    int w0 = -64;                              // first block of the cutoff window (none yet)
+    bool touched = !(FLAGS & EF_CUT);          // some block of this super-row ran (flush needed)
     for (int c = 0; c < cnt; ++c) {
-        const bool dx = (J == 2 * K);          // see run_tile: entry / exit rotation of a DX block
-        typename P::JState js;
-        P::load_j(A, base, n, 32 * J + ((lane + (dx ? 1 : 0)) & 31), js);
-        typename P::Part ip;
-        ip.zero();
-        const BlockInfo bi = block_info(A, r, K, J, nb);
-        if (J >= 2 * K + 2) {
-            if (bi.far) run_tile<P, FLAGS, M_FULL, true>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
-            else run_tile<P, FLAGS, M_FULL, false>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
-        } else if (J == 2 * K) {
-            run_tile<P, FLAGS, M_DX, false>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
-        } else {
-            run_tile<P, FLAGS, M_DY, false>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
+        bool run = true, straddle = false;
+        if (FLAGS & EF_CUT) {
+            if (J < w0 || J >= w0 + 32) {
+                cut_window<P>(A, r, K, J, nb, lane, w_in, w_st);
+                w0 = J;
+            }
+            run = (w_in >> (J - w0)) & 1u;
+            straddle = (w_st >> (J - w0)) & 1u;
         }
-        P::fold_i(is, sa, lane, ip);
-        P::flush_j(A, base, n, 32 * J + ((lane + (dx ? 17 : 0)) & 31), js);
+        if (run) {
+            const bool dx = (J == 2 * K);      // see run_tile: entry / exit rotation of a DX block
+            typename P::JState js;
+            P::load_j(A, base, n, 32 * J + ((lane + (dx ? 1 : 0)) & 31), js);
+            typename P::Part ip;
+            ip.zero();
+            const BlockInfo bi = block_info<P>(A, r, K, J, nb);
+            if (J >= 2 * K + 2) {
+                if (bi.far && !straddle) run_tile<P, FLAGS, M_FULL, true>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
+                else if (straddle) run_tile<P, FS, M_FULL, false>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
+                else run_tile<P, FLAGS, M_FULL, false>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
+            } else if (J == 2 * K) {
+                if (straddle) run_tile<P, FS, M_DX, false>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
+                else run_tile<P, FLAGS, M_DX, false>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
+            } else {
+                if (straddle) run_tile<P, FS, M_DY, false>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
+                else run_tile<P, FLAGS, M_DY, false>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
+            }
+            P::fold_i(is, sa, lane, ip);
+            P::flush_j(A, base, n, 32 * J + ((lane + (dx ? 17 : 0)) & 31), js);
+            touched = true;
+        }
         if (c + 1 < cnt && ++J == nb) {
-            P::flush_i(A, r, base, n, 64 * K, lane, is, sa);
+            w0 = -64;
+            if (touched) P::flush_i(A, r, base, n, 64 * K, lane, is, sa);
+            touched = !(FLAGS & EF_CUT);
 #pragma unroll
             for (int q = 0; q < 2 * P::NQ; ++q) sa[32 * q + lane] = 0;
             if (++K == nk) {
@@ -747,9 +1013,38 @@ __device__ __forceinline__ void walk_task(const PairArgs& A, const int4 t, long 
             P::load_i(A, base, n, 64 * K, lane, is);
         }
     }
-    P::flush_i(A, r, base, n, 64 * K, lane, is, sa);
+    if (touched) P::flush_i(A, r, base, n, 64 * K, lane, is, sa);
 }
 
+
+// --- the pair-pass kernel --------------------------------------------------------
+// One warp per task.  MINB = 1 leaves the register count to the compiler;
+// MINB = 3 or 4 caps it so that three or four 256-thread blocks fit on an SM
+// (more warps, some spills).
+template <class P, int FLAGS, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_pairs(PairArgs A, const int4* __restrict__ tasks, int n_tasks) {
+    pdl_enter();
+    extern __shared__ long long s_acc[];
+    const int lane = threadIdx.x & 31;
+    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= n_tasks) return;
+    walk_task<P, FLAGS>(A, tasks[w], s_acc + (threadIdx.x >> 5) * P::NQ * 64, lane);
+}
+
+// Launch of pass policy P over a task list; MAXCAP limits the register caps
+// instantiated (a larger cap request takes the largest one available).
+template <class P, int FLAGS, int MAXCAP = 4>
+cudaError_t launch_pass(const PairArgs& a, const TaskList& t, int cap, int wpb, cudaStream_t s) {
+    if (t.n_tasks == 0) return cudaSuccess;
+    const int blocks = (t.n_tasks + wpb - 1) / wpb;
+    const size_t smem = (size_t)wpb * P::NQ * 64 * sizeof(long long);
+    const dim3 g(blocks), b(32 * wpb);
+    if constexpr (MAXCAP >= 4) {
+        if (cap >= 4) return launch_pdl(k_pairs<P, FLAGS, 4>, g, b, smem, s, a, t.d_tasks, t.n_tasks);
+    }
+    if (cap >= 3) return launch_pdl(k_pairs<P, FLAGS, 3>, g, b, smem, s, a, t.d_tasks, t.n_tasks);
+    return launch_pdl(k_pairs<P, FLAGS, 1>, g, b, smem, s, a, t.d_tasks, t.n_tasks);
+}
 
 // Bounding boxes of every 32-atom tile (one warp per tile): lo.xyz with the
 // largest a = rho - offset, hi.xyz with the largest screened radius s.
