@@ -45,7 +45,9 @@ MUFU_PER_PAIR = {"born": 1, "energy": 3, "chain": 1}
 PASS_NAMES = ["born", "energy", "chain"]
 
 
-WORKLOADS = ("eremd_8x2048", "diff_16x4096", "uneven_64", "grid_48x25000")
+WORKLOADS = ("eremd_8x2048", "diff_16x4096", "uneven_64", "grid_48x25000", "cutoff_1x100000")
+# GB with cutoffs: Born-radius cutoff and pair cutoff (A) of the cutoff workload
+CUTOFFS = {"cutoff_1x100000": dict(rgbmax=12.0, cut=12.0)}
 
 
 def workload(name="eremd_8x2048"):
@@ -60,7 +62,17 @@ def workload(name="eremd_8x2048"):
         return synth.config_uneven()
     if name == "grid_48x25000":
         return synth.config_grid()
+    if name == "cutoff_1x100000":
+        return synth.config_cutoff(100000)
     raise ValueError(name)
+
+
+def pairs_per_md_step(b, name):
+    """Pair terms of one force evaluation: all pairs, or with a pair cutoff
+    the pairs within it at the starting coordinates."""
+    import synth
+    cut = CUTOFFS.get(name, {}).get("cut", 0.0)
+    return synth.pairs_within(b, cut) if cut > 0 else b.pairs_per_eval()
 
 
 # ----------------------------------------------------------------------------------
@@ -363,7 +375,7 @@ def main():
     import paper_1803_09652_gb300 as pkg
     pkg.load()
 
-    params = pkg.default_params(rep_k=10.0, rep_sigma=2.5)
+    params = pkg.default_params(rep_k=10.0, rep_sigma=2.5, **CUTOFFS.get(args.workload, {}))
     b = workload(args.workload)
     S = Setup(pkg, b, dev, seed=1234 + rank, params=params)
     if not args.no_autotune:
@@ -371,7 +383,7 @@ def main():
     persistent = args.persistent
     S.ctx.set_persistent(persistent)
     stream = torch.cuda.current_stream()
-    pairs_md = b.pairs_per_eval()
+    pairs_md = pairs_per_md_step(b, args.workload)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
 
     for _ in range(args.warmup):
@@ -444,7 +456,7 @@ def main():
     # ---- plain form: one context per replica, direct launches, no graph ---------
     plain = None
     if not args.no_plain and rank == 0:
-        plain = plain_form(pkg, b, dev, params, n_bench=10)
+        plain = plain_form(pkg, b, dev, params, n_bench=10, pairs_md=pairs_md)
 
     # ---- end to end through host buffers ----------------------------------------
     e2e = end_to_end(pkg, S, dev, n_bench=max(2, min(5, args.steps)), pairs_md=pairs_md)
@@ -464,6 +476,9 @@ def main():
                        "atoms_total": b.n_atoms, "md_steps_per_step": MD_PER_STEP,
                        "mc_every": MC_EVERY, "exchange_every": EX_EVERY,
                        "pairs_per_md_step": pairs_md, "l2": "flushed between steps (256 MB write)",
+                       "cutoffs_A": CUTOFFS.get(args.workload),
+                       "pairs_counted": "within the pair cutoff at the start" if args.workload in CUTOFFS
+                       else "all pairs",
                        "tiles": list(S.ctx.tiles()), "reg_caps": list(S.ctx.reg_caps()),
                        "parallelism": "replicas batched on one GPU"},
             "replica_md_steps_per_s": rep_steps,
@@ -526,7 +541,7 @@ def read_traffic(name):
     return table.get(name)
 
 
-def plain_form(pkg, b, dev, params, n_bench):
+def plain_form(pkg, b, dev, params, n_bench, pairs_md):
     """Each replica in its own context, MD + MC one step at a time with direct
     launches (no graph, no batching); same arithmetic.  Exchanges are O(M)
     and left out of this form."""
@@ -552,7 +567,7 @@ def plain_form(pkg, b, dev, params, n_bench):
     torch.cuda.synchronize()
     ms = statistics.median(a.elapsed_time(c) for a, c in ev)      # per bench step
     s = ms / 1000.0
-    pairs = b.pairs_per_eval() * MD_PER_STEP
+    pairs = pairs_md * MD_PER_STEP
     return {"value": pairs / s, "unit": "pair-interactions/s", "ms_per_step": ms,
             "replica_md_steps_per_s": b.n_rep * MD_PER_STEP / s, "bench_steps": n_bench, "statistic": "median",
             "form": "one context per replica, direct launches per MD step, no graph"}

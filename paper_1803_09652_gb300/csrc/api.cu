@@ -214,9 +214,12 @@ int setup_persist(gb_ctx* c) {
 }
 
 int default_tpt(const gb_ctx* c) {
-    // about four warp tasks per resident warp slot of 152 SMs x 32 warps
+    // about four warp tasks per resident warp slot of 152 SMs x 32 warps; with
+    // a cutoff most blocks are skipped and the rest cluster along the diagonal,
+    // so tasks eight times shorter even out the warps' work
     const int64_t slots = 152LL * 32 * 4;
     int64_t t = (c->total_tiles + slots - 1) / slots;
+    if (c->p.rgbmax > 0.0f || c->p.cut > 0.0f) t = (t + 7) / 8;
     return (int)std::max<int64_t>(1, std::min<int64_t>(t, 256));
 }
 

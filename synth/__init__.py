@@ -364,6 +364,29 @@ def config_grid(n_pH: int = 6, n_E: int = 8, n: int = 25000, seed: int = 0) -> B
     return Batch(reps, pH=pH, E=E, name=f"grid_{n_pH}x{n_E}x{n}", E_ladder=E_l, pH_ladder=pH_l)
 
 
+def config_cutoff(n: int = 100000, seed: int = 0) -> Batch:
+    """One large chain (default 100,000 atoms) with the grid's 40-site mix, for
+    GB with cutoffs: a single replica at pH 4.6 and E = E0."""
+    rng = np.random.default_rng(seed + 77)
+    specs = [(1, int(rng.integers(8, 31)), 2) for _ in range(8)]
+    specs += [(0, int(rng.integers(8, 31)), int(rng.integers(2, 5))) for _ in range(32)]
+    rep = make_replica(n, seed, specs)
+    return Batch([rep], pH=np.array([4.6]), E=np.array([E0_REF_V]), name=f"cutoff_1x{n}")
+
+
+def pairs_within(batch: Batch, cut: float) -> int:
+    """Unordered pairs closer than `cut` in every replica (the pair terms a
+    cutoff keeps), counted with a k-d tree."""
+    from scipy.spatial import cKDTree
+    total = 0
+    for rep in batch.replicas:
+        if rep.n < 2:
+            continue
+        t = cKDTree(rep.xyz.astype(np.float64))
+        total += (int(t.count_neighbors(t, cut)) - rep.n) // 2
+    return total
+
+
 def random_batch(sizes: List[int], seed: int, sites: bool = True) -> Batch:
     """Small uneven batches for parity tests (ragged tails, tiny replicas)."""
     reps = []
