@@ -220,7 +220,7 @@ __device__ __forceinline__ f2 hct_cut_fr2(f2 r, f2 rinv, f2 a, f2 s, float rc) {
 // wholly past rc, masked lanes) give 0.
 __device__ __forceinline__ f2 log1pv(f2 x) { return make_float2(log1pf(x.x), log1pf(x.y)); }
 struct CutFar {
-    f2 x, iL, J1, B;
+    f2 x, iL, i1, J1, B;              // i1 = 1 / (1 + x)
     bool cx, cy;                      // w = rc - L (the cutoff limits the shells)
 };
 __device__ __forceinline__ CutFar hct_cut_far_terms(f2 r, f2 s, float rc) {
@@ -233,8 +233,8 @@ __device__ __forceinline__ CutFar hct_cut_far_terms(f2 r, f2 s, float rc) {
     c.cy = wc.y < s2.y;
     const f2 w = make_float2(fmaxf(0.0f, c.cx ? wc.x : s2.x), fmaxf(0.0f, c.cy ? wc.y : s2.y));
     c.x = mul2(w, c.iL);
-    const f2 i1 = rcp2(add2(F2(1.0f), c.x));
-    const f2 i12 = mul2(i1, i1);
+    c.i1 = rcp2(add2(F2(1.0f), c.x));
+    const f2 i12 = mul2(c.i1, c.i1);
     c.J1 = mul2(mul2(F2(0.5f), mul2(c.x, c.x)), i12);
     const f2 J2 = add2(log1pv(c.x), neg2(mul2(mul2(mul2(F2(0.5f), c.x), fma2(F2(3.0f), c.x, F2(2.0f))), i12)));
     c.B = fma2(mul2(s2, c.iL), c.J1, neg2(J2));
@@ -250,7 +250,7 @@ __device__ __forceinline__ f2 hct_cut_far2(f2 r, f2 rinv, f2 s, float rc) {
 __device__ __forceinline__ f2 hct_cut_far_fr2(f2 r, f2 rinv, f2 s, float rc) {
     const CutFar c = hct_cut_far_terms(r, s, rc);
     const f2 s2 = add2(s, s);
-    const f2 i1 = rcp2(add2(F2(1.0f), c.x));
+    const f2 i1 = c.i1;
     const f2 xp = mul2(neg2(c.iL), make_float2(c.cx ? 1.0f + c.x.x : c.x.x, c.cy ? 1.0f + c.x.y : c.x.y));
     const f2 t = mul2(mul2(mul2(xp, c.x), fma2(s2, c.iL, neg2(c.x))), mul2(mul2(i1, i1), i1));
     const f2 dB = fma2(neg2(mul2(s2, mul2(c.iL, c.iL))), c.J1, t);
@@ -373,6 +373,24 @@ struct Born {
         const f2 rinv2 = mul2(rinv, rinv), rinv4 = mul2(rinv2, rinv2);
         const float sj2 = j.s * j.s;
         const f2 y_ij = mul2(F2(sj2), rinv2), y_ji = mul2(i.s2, rinv2);
+        // EF_STRADDLE: lanes whose sphere lies wholly past rgbmax give 0; a step
+        // with some sphere across it takes the restricted form for every lane
+        bool out_ij0 = false, out_ij1 = false, out_ji0 = false, out_ji1 = false;
+        if (FLAGS & EF_STRADDLE) {
+            const f2 r = mul2(r2, rinv);
+            const float rc = A.rgbmax;
+            out_ij0 = r.x - j.s >= rc; out_ij1 = r.y - j.s >= rc;
+            out_ji0 = r.x - i.s.x >= rc; out_ji1 = r.y - i.s.y >= rc;
+            const bool sh = (!out_ij0 && r.x + j.s > rc) || (!out_ij1 && r.y + j.s > rc) ||
+                            (!out_ji0 && r.x + i.s.x > rc) || (!out_ji1 && r.y + i.s.y > rc);
+            if (__any_sync(0xffffffffu, sh)) {
+                const f2 h_ij = keep<MODE>(hct_cut_dir2(r, rinv, i.a, F2(j.s), rc), m);
+                const f2 h_ji = keep<MODE>(hct_cut_dir2(r, rinv, F2(j.a), i.s, rc), m);
+                p.I = add2(p.I, h_ij);
+                j.acc += h_ji.x + h_ji.y;
+                return;
+            }
+        }
         if (FAR) {  // whole block proven disjoint and far: no votes, short polynomial
             p.I = fma2(F2(0.5f * sj2 * j.s), mul2(rinv4, gb_poly_gf2(y_ij)), p.I);
             const f2 h = mul2(i.hs3, mul2(rinv4, gb_poly_gf2(y_ji)));
@@ -407,19 +425,9 @@ struct Born {
                 h_ji = make_float2(c0 ? hc.x : h_ji.x, c1 ? hc.y : h_ji.y);
             }
         }
-        if (FLAGS & EF_STRADDLE) {   // directions whose sphere reaches past rgbmax
-            const f2 r = mul2(r2, rinv);
-            const float rc = A.rgbmax;
-            const bool u0 = r.x + j.s > rc, u1 = r.y + j.s > rc;
-            const bool v0 = r.x + i.s.x > rc, v1 = r.y + i.s.y > rc;
-            if (__any_sync(0xffffffffu, u0 || u1)) {
-                const f2 hc = hct_cut_dir2(r, rinv, i.a, F2(j.s), rc);
-                h_ij = make_float2(u0 ? hc.x : h_ij.x, u1 ? hc.y : h_ij.y);
-            }
-            if (__any_sync(0xffffffffu, v0 || v1)) {
-                const f2 hc = hct_cut_dir2(r, rinv, F2(j.a), i.s, rc);
-                h_ji = make_float2(v0 ? hc.x : h_ji.x, v1 ? hc.y : h_ji.y);
-            }
+        if (FLAGS & EF_STRADDLE) {   // no sphere across rgbmax: wholly inside or past it
+            h_ij = make_float2(out_ij0 ? 0.0f : h_ij.x, out_ij1 ? 0.0f : h_ij.y);
+            h_ji = make_float2(out_ji0 ? 0.0f : h_ji.x, out_ji1 ? 0.0f : h_ji.y);
         }
         h_ij = keep<MODE>(h_ij, m);
         h_ji = keep<MODE>(h_ji, m);
@@ -691,6 +699,26 @@ struct Chain {
         const f2 rinv2 = mul2(rinv, rinv);
         const float sj2 = j.s * j.s;
         const f2 y_ij = mul2(F2(sj2), rinv2), y_ji = mul2(i.s2, rinv2);
+        // EF_STRADDLE: as in Born; a lane with one direction wholly past rgbmax
+        // has the other across it or past it too
+        bool out0 = false, out1 = false;
+        if (FLAGS & EF_STRADDLE) {
+            const f2 r = mul2(r2, rinv);
+            const float rc = A.rgbmax;
+            out0 = r.x - j.s >= rc && r.x - i.s.x >= rc;
+            out1 = r.y - j.s >= rc && r.y - i.s.y >= rc;
+            const bool sh = (!out0 && (r.x + j.s > rc || r.x + i.s.x > rc)) ||
+                            (!out1 && (r.y + j.s > rc || r.y + i.s.y > rc));
+            if (__any_sync(0xffffffffu, sh)) {
+                const f2 fr = keep<MODE>(fma2(i.c, hct_cut_dir_fr2(r, rinv, i.a, F2(j.s), rc),
+                                              mul2(F2(j.c), hct_cut_dir_fr2(r, rinv, F2(j.a), i.s, rc))), m);
+                p.sx = fma2(fr, dx, p.sx); p.sy = fma2(fr, dy, p.sy); p.sz = fma2(fr, dz, p.sz);
+                j.fx = fmaf(fr.y, dx.y, fmaf(fr.x, dx.x, j.fx));
+                j.fy = fmaf(fr.y, dy.y, fmaf(fr.x, dy.x, j.fy));
+                j.fz = fmaf(fr.y, dz.y, fmaf(fr.x, dz.x, j.fz));
+                return;
+            }
+        }
         if (FAR) {  // whole block proven disjoint and far: no votes, short polynomial
             const f2 t = fma2(mul2(i.c, F2(0.5f * sj2 * j.s)), gb_poly_hf2(y_ij),
                               mul2(mul2(F2(j.c), i.hs3), gb_poly_hf2(y_ji)));
@@ -732,16 +760,7 @@ struct Chain {
             const f2 fbc = add2(fb, fc);
             fr = make_float2(b0 || c0 ? fbc.x : fr.x, b1 || c1 ? fbc.y : fr.y);
         }
-        if (FLAGS & EF_STRADDLE) {   // a direction reaches past rgbmax: both from the cut form
-            const f2 r = mul2(r2, rinv);
-            const float rc = A.rgbmax;
-            const bool u0 = r.x + j.s > rc || r.x + i.s.x > rc, u1 = r.y + j.s > rc || r.y + i.s.y > rc;
-            if (__any_sync(0xffffffffu, u0 || u1)) {
-                const f2 fbc = fma2(i.c, hct_cut_dir_fr2(r, rinv, i.a, F2(j.s), rc),
-                                    mul2(F2(j.c), hct_cut_dir_fr2(r, rinv, F2(j.a), i.s, rc)));
-                fr = make_float2(u0 ? fbc.x : fr.x, u1 ? fbc.y : fr.y);
-            }
-        }
+        if (FLAGS & EF_STRADDLE) fr = make_float2(out0 ? 0.0f : fr.x, out1 ? 0.0f : fr.y);
         fr = keep<MODE>(fr, m);
         p.sx = fma2(fr, dx, p.sx); p.sy = fma2(fr, dy, p.sy); p.sz = fma2(fr, dz, p.sz);
         j.fx = fmaf(fr.y, dx.y, fmaf(fr.x, dx.x, j.fx));
