@@ -301,7 +301,7 @@ def site_reference_energies_gpu(pkg, batch, dev, params):
     return G
 
 
-def launches_per_segment(md_steps, persistent=True):
+def launches_per_segment(md_steps, persistent=True, cutoff=False):
     """Kernels of this library enqueued by one gb_md_segment call of md_steps."""
     n_mc = md_steps // MC_EVERY
     mc = 4 * n_mc                                  # (slice rows + decision) x (protonation, redox)
@@ -309,9 +309,10 @@ def launches_per_segment(md_steps, persistent=True):
     if persistent:
         md = n_mc                                  # one persistent launch per run between MC points
     else:
-        # per step: 3 pair passes, 2 transforms, one close-and-open launch;
+        # per step: 3 pair passes, 2 transforms, one close-and-open launch
+        # (with a cutoff also the list reset and the block-list build);
         # plus the opening half step of the segment
-        md = 6 * md_steps + 1
+        md = (8 if cutoff else 6) * md_steps + 1
     return 1 + md + mc + ex + 1                    # + set counters, + advance step counter
 
 
@@ -494,9 +495,10 @@ def main():
             "plain": plain,
             "e2e": e2e,
             "cpu_baseline": cpu,
-            "gpu_launches": launches_per_segment(MD_PER_STEP, persistent) * args.steps,
+            "gpu_launches": launches_per_segment(MD_PER_STEP, persistent, args.workload in CUTOFFS) * args.steps,
             "md_kernel": "persistent (one launch per run between MC points)" if persistent else
-                         "six launches per MD step",
+                         ("eight launches per MD step (block neighbour list)" if args.workload in CUTOFFS
+                          else "six launches per MD step"),
             "clocks": clk,
             "wall_s_timed": wall,
         }

@@ -33,6 +33,12 @@ struct gb_ctx {
     double* sweep_part = nullptr;       // the same for per-residue sweeps (allocated on first use)
     float4* boxes = nullptr;            // tile bounding boxes
     int* tile_off = nullptr;
+    // block neighbour lists of the cutoffs (allocated only with a cutoff)
+    int4* list_b = nullptr;             // Born-radius cutoff: Born and chain passes
+    int4* list_e = nullptr;             // pair cutoff: energy pass
+    int* list_ctr = nullptr;            // [gbk::LIST_CTRS] lengths and queue heads
+    int* win_off = nullptr;             // [M+1] first list-building warp of each replica
+    int list_warps = 0;
     int n_tiles32 = 0;
     int32_t mc_parts = 0;
     gbk::TaskList tasks;
@@ -282,6 +288,15 @@ cudaError_t mark(gb_ctx* c, cudaEvent_t e, cudaStream_t s) {
     return c->capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
 }
 
+// One pair pass: over the static task list, or with the pass's cutoff over
+// its block neighbour list (built by launch_block_list for this evaluation).
+cudaError_t pass(const gb_ctx* c, int which, int flags, const gbk::PairArgs& pa, cudaStream_t s) {
+    const int4* list = (which == gbk::PASS_ENERGY) ? c->list_e : c->list_b;
+    if (list) return gbk::launch_pairs_list(which, flags | gbk::EF_CUT, pa, list, c->list_ctr, c->tasks.cap[which],
+                                            c->wpb, s);
+    return gbk::launch_pairs(which, flags, pa, c->tasks, c->wpb, s);
+}
+
 // md != null: an MD step; the chain-bond forces join the force accumulators
 // and the tile boxes were already built by k_md_step (build_boxes false).
 int evaluate(gb_ctx* c, const float* xyzq, const float* rad, float* R_out, int flags,
@@ -291,18 +306,20 @@ int evaluate(gb_ctx* c, const float* xyzq, const float* rad, float* R_out, int f
     const gbk::PairArgs pa = pair_args(c, xyzq, rad);
     const gbk::AtomArgs aa = atom_args(c, xyzq, rad);
     if (build_boxes) GB_CHECK(c, gbk::launch_tile_boxes(pa, c->M, c->n_tiles32, s));
+    if (c->list_ctr)
+        GB_CHECK(c, gbk::launch_block_list(pa, c->win_off, c->M, c->list_warps, c->list_b, c->list_e, c->list_ctr,
+                                           c->list_b ? 1 : 0, c->list_e ? 1 : 0, s));
     if (ev) GB_CHECK(c, mark(c, ev[0], s));
-    GB_CHECK(c, gbk::launch_pairs(gbk::PASS_BORN, gbk::cut_flag(gbk::PASS_BORN, c->p), pa, c->tasks, c->wpb, s));
+    GB_CHECK(c, pass(c, gbk::PASS_BORN, 0, pa, s));
     if (ev) GB_CHECK(c, mark(c, ev[1], s));
     GB_CHECK(c, gbk::launch_born_finalize(aa, R_out, s));
     if (ev) GB_CHECK(c, mark(c, ev[2], s));
-    GB_CHECK(c, gbk::launch_pairs(gbk::PASS_ENERGY, flags | gbk::cut_flag(gbk::PASS_ENERGY, c->p), pa, c->tasks,
-                                  c->wpb, s));
+    GB_CHECK(c, pass(c, gbk::PASS_ENERGY, flags, pa, s));
     if (ev) GB_CHECK(c, mark(c, ev[3], s));
     GB_CHECK(c, gbk::launch_energy_finalize(aa, (flags & gbk::EF_ENERGY) ? 1 : 0, phi_out, s,
                                             md ? md->bond_k : 0.0f, md ? md->bond_r0 : 0.0f));
     if (ev) GB_CHECK(c, mark(c, ev[4], s));
-    GB_CHECK(c, gbk::launch_pairs(gbk::PASS_CHAIN, gbk::cut_flag(gbk::PASS_CHAIN, c->p), pa, c->tasks, c->wpb, s));
+    GB_CHECK(c, pass(c, gbk::PASS_CHAIN, 0, pa, s));
     if (ev) GB_CHECK(c, mark(c, ev[5], s));
     return GB_OK;
 }
@@ -383,6 +400,22 @@ extern "C" int gb_ctx_create(gb_ctx** out, int32_t n_rep, const int64_t* atom_of
         if (e == cudaSuccess)
             e = cudaMemcpy(c->tile_off, toff.data(), sizeof(int) * (n_rep + 1), cudaMemcpyHostToDevice);
         step(zalloc(&c->boxes, 2 * (size_t)std::max(c->n_tiles32, 1)));
+        if (params->rgbmax > 0.0f || params->cut > 0.0f) {
+            // every block of the batch may be in range: one task of one block each
+            std::vector<int> woff(n_rep + 1, 0);
+            for (int r = 0; r < n_rep; ++r) {
+                const int64_t nb = (atom_off[r + 1] - atom_off[r] + 31) / 32;
+                woff[r + 1] = woff[r] + (int)(((nb + 1) / 2) * ((nb + 31) / 32));
+            }
+            c->list_warps = woff[n_rep];
+            const size_t cap = (size_t)std::max<int64_t>(c->total_tiles, 1);
+            if (params->rgbmax > 0.0f) step(zalloc(&c->list_b, cap));
+            if (params->cut > 0.0f) step(zalloc(&c->list_e, cap));
+            step(zalloc(&c->list_ctr, gbk::LIST_CTRS));
+            step(zalloc(&c->win_off, n_rep + 1));
+            if (e == cudaSuccess)
+                e = cudaMemcpy(c->win_off, woff.data(), sizeof(int) * (n_rep + 1), cudaMemcpyHostToDevice);
+        }
     }
     step(zalloc(&c->mc_part, (size_t)n_rep * std::max(c->mc_parts, 1) * gbk::MC_MAX_SITE_ATOMS));
     step(cudaStreamCreateWithFlags(&c->cs, cudaStreamNonBlocking));
@@ -432,6 +465,10 @@ extern "C" int gb_ctx_destroy(gb_ctx* c) {
     cudaFree(c->mc_part);
     cudaFree(c->sweep_part);
     cudaFree(c->boxes);
+    cudaFree(c->list_b);
+    cudaFree(c->list_e);
+    cudaFree(c->list_ctr);
+    cudaFree(c->win_off);
     cudaFree(c->tile_off);
     if (c->cs) cudaStreamDestroy(c->cs);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
@@ -512,7 +549,10 @@ extern "C" int gb_born_radii(gb_ctx* c, const float* xyzq, const float* rad, flo
     const gbk::PairArgs pa = pair_args(c, xyzq, rad);
     const gbk::AtomArgs aa = atom_args(c, xyzq, rad);
     GB_CHECK(c, gbk::launch_tile_boxes(pa, c->M, c->n_tiles32, s));
-    GB_CHECK(c, gbk::launch_pairs(gbk::PASS_BORN, gbk::cut_flag(gbk::PASS_BORN, c->p), pa, c->tasks, c->wpb, s));
+    if (c->list_b)
+        GB_CHECK(c, gbk::launch_block_list(pa, c->win_off, c->M, c->list_warps, c->list_b, nullptr, c->list_ctr, 1, 0,
+                                           s));
+    GB_CHECK(c, pass(c, gbk::PASS_BORN, 0, pa, s));
     GB_CHECK(c, gbk::launch_born_finalize(aa, R_out, s));
     return GB_OK;
 }

@@ -49,16 +49,27 @@ struct TaskList {
 enum PassKind { PASS_BORN = 0, PASS_ENERGY = 1, PASS_CHAIN = 2 };
 
 // flags for the energy pass; EF_CUT for any pass: the kernel applies the
-// pass's cutoff (Born and chain passes: rgbmax; energy pass: cut), skipping
-// out-of-range blocks.  EF_STRADDLE is internal to the walker: the block has
-// pairs on both sides of the cutoff and tests each pair.
+// pass's cutoff (Born and chain passes: rgbmax; energy pass: cut) to a task
+// list of in-range blocks (launch_pairs_list).  EF_STRADDLE is internal to
+// the walker: the block has pairs on both sides of the cutoff and tests each
+// pair.
 enum { EF_ENERGY = 1, EF_PHI = 2, EF_REP = 4, EF_SALT = 8, EF_CUT = 16, EF_STRADDLE = 32 };
 
 cudaError_t launch_pairs(int pass, int flags, const PairArgs& a, const TaskList& t,
                          int warps_per_block, cudaStream_t s);
-// the EF_CUT kernels (pairs_cut.cu); launch_pairs forwards to it
-cudaError_t launch_pairs_cut(int pass, int flags, const PairArgs& a, const TaskList& t,
-                             int warps_per_block, cudaStream_t s);
+// Cutoff passes (pairs_cut.cu).  launch_block_list clears the LIST_CTRS
+// counters and builds the block neighbour lists from the tile boxes: list_b
+// (Born-radius cutoff, when want_b) and list_e (pair cutoff, when want_e),
+// each with room for every block of the batch; win_off [M+1] holds the first
+// list-building warp of each replica (ceil(nb/2) * ceil(nb/32) warps per
+// replica of nb tiles).  launch_pairs_list runs pass `pass` with EF_CUT over
+// a device-built task list whose length is ctr[0] (Born, chain) or ctr[1]
+// (energy), taking tasks from the queue head ctr[2 + pass].
+constexpr int LIST_CTRS = 5;
+cudaError_t launch_block_list(const PairArgs& a, const int* win_off, int M, int total_warps, int4* list_b,
+                              int4* list_e, int* ctr, int want_b, int want_e, cudaStream_t s);
+cudaError_t launch_pairs_list(int pass, int flags, const PairArgs& a, const int4* list, int* ctr, int cap,
+                              int warps_per_block, cudaStream_t s);
 
 // Cutoff fields of the pair arguments, and the EF_CUT flag of each pass.
 inline void set_cutoffs(PairArgs& a, const gb_params& p) {

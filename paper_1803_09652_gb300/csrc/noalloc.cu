@@ -41,7 +41,8 @@ constexpr size_t kOffCfac = kOffRh + align256(8ull * kMaxAtoms);               /
 constexpr size_t kOffCc = kOffCfac + align256(4ull * kMaxAtoms);               // float[max]
 constexpr size_t kOffOff = kOffCc + align256(4ull * kMaxAtoms);                // int64[2]
 constexpr size_t kOffErr = kOffOff + 256;                                      // int
-constexpr size_t kOffTasks = kOffErr + 256;                                    // int4[max tasks]
+constexpr size_t kOffCtr = kOffErr + 256;                                      // int[LIST_CTRS]
+constexpr size_t kOffTasks = kOffCtr + 256;                                    // int4[max tasks]
 constexpr size_t kBytes = kOffTasks + align256(16ull * kMaxTasks);
 
 __device__ __align__(256) unsigned char gb_static_scratch[kBytes];
@@ -69,12 +70,15 @@ int scratch_for_current_device(unsigned char** out) {
 // pair walk (super-rows K of 64 atoms against tiles J = 2K .. nb-1).  Also
 // writes atom_off = {0, n}.
 __global__ void k_static_tasks(int n, int nb, int tpt, int n_tasks, int64_t total, int4* tasks,
-                               int64_t* atom_off) {
+                               int64_t* atom_off, int* ctr) {
     gbk::pdl_enter();
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w == 0) {
         atom_off[0] = 0;
         atom_off[1] = n;
+        // the cutoff passes walk this list from a queue: lengths, cleared heads
+        ctr[0] = ctr[1] = n_tasks;
+        ctr[2] = ctr[3] = ctr[4] = 0;
     }
     if (w >= n_tasks) return;
     int64_t p = (int64_t)w * tpt;
@@ -117,12 +121,13 @@ extern "C" int gb_energy_forces_static(int32_t n_atoms, const gb_params* params,
     float* cc = (float*)(base + kOffCc);
     int64_t* atom_off = (int64_t*)(base + kOffOff);
     int* err = (int*)(base + kOffErr);
+    int* ctr = (int*)(base + kOffCtr);
     int4* tasks = (int4*)(base + kOffTasks);
 
     // the accumulators keep the last call's contents: start from zero
     if (cudaMemsetAsync(base, 0, kAccEnd, s) != cudaSuccess) return GB_ERR_CUDA;
     if (gbk::launch_pdl(k_static_tasks, dim3((n_tasks + 255) / 256), dim3(256), 0, s, n, nb, kTilesPerTask, n_tasks,
-                        total, tasks, atom_off) != cudaSuccess)
+                        total, tasks, atom_off, ctr) != cudaSuccess)
         return GB_ERR_CUDA;
 
     gbk::PairArgs pa{};
@@ -177,16 +182,19 @@ extern "C" int gb_energy_forces_static(int32_t n_atoms, const gb_params* params,
     const int flags = (E_out ? gbk::EF_ENERGY : 0) | (dEdq_out ? gbk::EF_PHI : 0) |
                       (params->rep_k != 0.0f ? gbk::EF_REP : 0) | (params->kappa != 0.0f ? gbk::EF_SALT : 0);
     const int wpb = 8;
+    // with a cutoff a pass walks the same task list from a queue, testing
+    // every pair (no boxes here, so no block is proven in or out of range)
     const gb_params& P = *params;
-    if (gbk::launch_pairs(gbk::PASS_BORN, gbk::cut_flag(gbk::PASS_BORN, P), pa, tl, wpb, s) != cudaSuccess)
-        return GB_ERR_CUDA;
+    auto pass = [&](int which, int f) {
+        if (gbk::cut_flag(which, P))
+            return gbk::launch_pairs_list(which, f | gbk::EF_CUT, pa, tasks, ctr, 3, wpb, s);
+        return gbk::launch_pairs(which, f, pa, tl, wpb, s);
+    };
+    if (pass(gbk::PASS_BORN, 0) != cudaSuccess) return GB_ERR_CUDA;
     if (gbk::launch_born_finalize(aa, R_out, s) != cudaSuccess) return GB_ERR_CUDA;
-    if (gbk::launch_pairs(gbk::PASS_ENERGY, flags | gbk::cut_flag(gbk::PASS_ENERGY, P), pa, tl, wpb, s) !=
-        cudaSuccess)
-        return GB_ERR_CUDA;
+    if (pass(gbk::PASS_ENERGY, flags) != cudaSuccess) return GB_ERR_CUDA;
     if (gbk::launch_energy_finalize(aa, E_out ? 1 : 0, dEdq_out, s) != cudaSuccess) return GB_ERR_CUDA;
-    if (gbk::launch_pairs(gbk::PASS_CHAIN, gbk::cut_flag(gbk::PASS_CHAIN, P), pa, tl, wpb, s) != cudaSuccess)
-        return GB_ERR_CUDA;
+    if (pass(gbk::PASS_CHAIN, 0) != cudaSuccess) return GB_ERR_CUDA;
     if (gbk::launch_forces_out(aa, F_fixed, F_out, E_out, s) != cudaSuccess) return GB_ERR_CUDA;
     return GB_OK;
 }

@@ -1,6 +1,7 @@
-// Launchers of the O(N^2) pair passes without cutoffs (those with a cutoff are
-// in pairs_cut.cu); the pass arithmetic, the warp walk and the kernel template
-// are in pairs_impl.cuh (shared with the persistent MD kernel).
+// Launchers of the O(N^2) pair passes without cutoffs (the block neighbour
+// list and the passes with a cutoff are in pairs_cut.cu); the pass
+// arithmetic, the warp walk and the kernel templates are in pairs_impl.cuh
+// (shared with the persistent MD kernel).
 #include "pairs_impl.cuh"
 
 namespace gbk {
@@ -20,7 +21,7 @@ cudaError_t launch_tile_boxes(const PairArgs& a, int M, int total_tiles, cudaStr
 
 cudaError_t launch_pairs(int pass, int flags, const PairArgs& a, const TaskList& t, int wpb,
                          cudaStream_t s) {
-    if (flags & EF_CUT) return launch_pairs_cut(pass, flags, a, t, wpb, s);
+    if (flags & EF_CUT) return cudaErrorInvalidValue;     // cutoff passes: launch_pairs_list
     const int cap = t.cap[pass];
     if (pass == PASS_BORN) return launch_pass<Born, 0>(a, t, cap, wpb, s);
     if (pass == PASS_CHAIN) return launch_pass<Chain, 0>(a, t, cap, wpb, s);

@@ -296,6 +296,7 @@ enum { M_FULL = 0, M_DX = 1, M_DY = 2 };
 // far-field form valid for both directions of a pair.
 struct BlockInfo {
     bool far;
+    bool straddle;    // EF_CUT kernels: some pairs of the block on each side of the cutoff
     float t_near;
     float skip2;      // EF_STRADDLE blocks: a step whose pairs all have r^2 > skip2 adds nothing
 };
@@ -861,97 +862,91 @@ __device__ __forceinline__ void run_tile(const PairArgs& A, const typename P::IS
 // directions of a pair disjoint with (s/r)^2 <= YMAX (far-field form valid),
 // so only steps with a closer pair need the exact tests.  Without boxes
 // nothing is proven.
+// Bounds between the box of super-row K (tiles 2K, 2K+1) and the box of tile
+// J: least and greatest distance squared, largest a and largest s of both.
+struct BoxPair {
+    float rmin2, rmax2, amax, smax;
+};
+__device__ __forceinline__ float4 row_box_lo(const PairArgs& A, int t0, int K, int nb, float4* hi) {
+    float4 il = __ldcg(&A.boxes[2 * (t0 + 2 * K)]), ih = __ldcg(&A.boxes[2 * (t0 + 2 * K) + 1]);
+    if (2 * K + 1 < nb) {
+        const float4 l1 = __ldcg(&A.boxes[2 * (t0 + 2 * K + 1)]), h1 = __ldcg(&A.boxes[2 * (t0 + 2 * K + 1) + 1]);
+        il = make_float4(fminf(il.x, l1.x), fminf(il.y, l1.y), fminf(il.z, l1.z), fmaxf(il.w, l1.w));
+        ih = make_float4(fmaxf(ih.x, h1.x), fmaxf(ih.y, h1.y), fmaxf(ih.z, h1.z), fmaxf(ih.w, h1.w));
+    }
+    *hi = ih;
+    return il;
+}
+__device__ __forceinline__ BoxPair box_pair(float4 il, float4 ih, float4 jl, float4 jh) {
+    BoxPair b;
+    const float gx = fmaxf(0.0f, fmaxf(il.x - jh.x, jl.x - ih.x));
+    const float gy = fmaxf(0.0f, fmaxf(il.y - jh.y, jl.y - ih.y));
+    const float gz = fmaxf(0.0f, fmaxf(il.z - jh.z, jl.z - ih.z));
+    const float mx = fmaxf(ih.x - jl.x, jh.x - il.x);
+    const float my = fmaxf(ih.y - jl.y, jh.y - il.y);
+    const float mz = fmaxf(ih.z - jl.z, jh.z - il.z);
+    b.rmin2 = gx * gx + gy * gy + gz * gz;
+    b.rmax2 = mx * mx + my * my + mz * mz;
+    b.amax = fmaxf(il.w, jl.w);
+    b.smax = fmaxf(ih.w, jh.w);
+    return b;
+}
+
+// Cutoff classes of a block from its box bounds (rmin / rmax the least /
+// greatest distance between the boxes, smax the largest screened radius):
+//   Born-radius cutoff (Born and chain passes): in range when
+//     rmin < rgbmax + smax (some sphere j reaches into the ball about some
+//     i), straddling when rmax + smax > rgbmax (some sphere reaches past it);
+//   pair cutoff (energy pass): in range when rmin <= max(cut, rep_sigma),
+//     straddling when rmax > cut.
+// The bounds carry a 0.1 % margin, so that FP32 rounding of a pair's r^2 can
+// never move it across a decision taken for its block.  A block that is not
+// straddling needs no per-pair test; one out of range adds nothing.
+__device__ __forceinline__ void cut_class(const PairArgs& A, bool radius_cut, const BoxPair& b, bool& in,
+                                          bool& st) {
+    if (radius_cut) {
+        const float reach = A.rgbmax + b.smax, inner = A.rgbmax - b.smax;
+        in = b.rmin2 <= 1.001f * reach * reach;
+        st = inner <= 0.0f || b.rmax2 >= 0.999f * inner * inner;
+    } else {
+        in = b.rmin2 <= 1.001f * A.e_range2;
+        st = b.rmax2 >= 0.999f * A.cut2;
+    }
+}
+
 template <class P>
 __device__ __forceinline__ BlockInfo block_info(const PairArgs& A, int r, int K, int J, int nb) {
     BlockInfo bi;
     bi.skip2 = INFINITY;
-    if (!A.boxes) {
+    if (!A.boxes) {   // nothing proven: near, and straddling when a cutoff is applied
         bi.far = false;
+        bi.straddle = true;
         bi.t_near = INFINITY;
         return bi;
     }
     const int t0 = A.tile_off[r];
     const float4 jl = __ldcg(&A.boxes[2 * (t0 + J)]), jh = __ldcg(&A.boxes[2 * (t0 + J) + 1]);
-    float4 il = __ldcg(&A.boxes[2 * (t0 + 2 * K)]), ih = __ldcg(&A.boxes[2 * (t0 + 2 * K) + 1]);
-    if (2 * K + 1 < nb) {
-        const float4 l1 = __ldcg(&A.boxes[2 * (t0 + 2 * K + 1)]), h1 = __ldcg(&A.boxes[2 * (t0 + 2 * K + 1) + 1]);
-        il = make_float4(fminf(il.x, l1.x), fminf(il.y, l1.y), fminf(il.z, l1.z), fmaxf(il.w, l1.w));
-        ih = make_float4(fmaxf(ih.x, h1.x), fmaxf(ih.y, h1.y), fmaxf(ih.z, h1.z), fmaxf(ih.w, h1.w));
-    }
-    const float gx = fmaxf(0.0f, fmaxf(il.x - jh.x, jl.x - ih.x));
-    const float gy = fmaxf(0.0f, fmaxf(il.y - jh.y, jl.y - ih.y));
-    const float gz = fmaxf(0.0f, fmaxf(il.z - jh.z, jl.z - ih.z));
-    const float rmin2 = gx * gx + gy * gy + gz * gz;
-    const float amax = fmaxf(il.w, jl.w), smax = fmaxf(ih.w, jh.w);
-    const float as = amax + smax;
-    bi.far = rmin2 >= as * as && smax * smax <= GB_POLY_YFAR * rmin2;
-    if (A.rep_k != 0.0f) bi.far = bi.far && rmin2 >= A.rep_sigma * A.rep_sigma;
+    float4 ih;
+    const float4 il = row_box_lo(A, t0, K, nb, &ih);
+    const BoxPair b = box_pair(il, ih, jl, jh);
+    const float as = b.amax + b.smax;
+    bi.far = b.rmin2 >= as * as && b.smax * b.smax <= GB_POLY_YFAR * b.rmin2;
+    if (A.rep_k != 0.0f) bi.far = bi.far && b.rmin2 >= A.rep_sigma * A.rep_sigma;
     // thresholds rounded up a little, so that rounding in r^2 cannot admit a
     // pair the exact test would reject
-    bi.t_near = 1.0001f * fmaxf(as * as, smax * smax * (1.0f / GB_POLY_YMAX));
-    // past the cutoff's reach (a pair wholly beyond adds exact zeros): Born and
-    // chain passes r >= rgbmax + s for both spheres, energy pass r > max(cut, rep_sigma)
+    bi.t_near = 1.0001f * fmaxf(as * as, b.smax * b.smax * (1.0f / GB_POLY_YMAX));
+    // EF_CUT kernels: the block's cutoff class, and the reach past which a
+    // pair adds exact zeros (Born and chain passes r >= rgbmax + s for both
+    // spheres, energy pass r > max(cut, rep_sigma))
+    bool in;
+    cut_class(A, P::RADIUS_CUT, b, in, bi.straddle);
     if (P::RADIUS_CUT) {
-        const float reach = A.rgbmax + smax;
+        const float reach = A.rgbmax + b.smax;
         bi.skip2 = 1.001f * reach * reach;
     } else {
         bi.skip2 = 1.001f * A.e_range2;
     }
     return bi;
-}
-
-// Cutoff window (EF_CUT kernels): lane l classifies block (K, J0 + l) from the
-// tile bounding boxes, and two ballots give the warp the in-range and the
-// straddle bits of 32 consecutive blocks of the super-row at once.  With
-// rmin / rmax the least / greatest distance between the super-row's box and
-// the tile's box and smax the largest screened radius in either:
-//   Born and chain passes (rgbmax): in range when rmin < rgbmax + smax (some
-//     sphere j reaches into the ball about some i), straddling when
-//     rmax + smax > rgbmax (some sphere reaches past it);
-//   energy pass (cut): in range when rmin <= max(cut, rep_sigma), straddling
-//     when rmax > cut.
-// The bounds carry a 0.1 % margin, so that FP32 rounding of a pair's r^2 can
-// never move it across a decision taken for its block.  A block that is not
-// straddling needs no per-pair test; one out of range is skipped.  Without
-// boxes every block is in range and straddling.
-template <class P>
-__device__ __forceinline__ void cut_window(const PairArgs& A, int r, int K, int J0, int nb, int lane,
-                                           unsigned& in_mask, unsigned& st_mask) {
-    if (!A.boxes) {
-        in_mask = st_mask = 0xffffffffu;
-        return;
-    }
-    const int t0 = A.tile_off[r];
-    float4 il = __ldcg(&A.boxes[2 * (t0 + 2 * K)]), ih = __ldcg(&A.boxes[2 * (t0 + 2 * K) + 1]);
-    if (2 * K + 1 < nb) {
-        const float4 l1 = __ldcg(&A.boxes[2 * (t0 + 2 * K + 1)]), h1 = __ldcg(&A.boxes[2 * (t0 + 2 * K + 1) + 1]);
-        il = make_float4(fminf(il.x, l1.x), fminf(il.y, l1.y), fminf(il.z, l1.z), fmaxf(il.w, l1.w));
-        ih = make_float4(fmaxf(ih.x, h1.x), fmaxf(ih.y, h1.y), fmaxf(ih.z, h1.z), fmaxf(ih.w, h1.w));
-    }
-    const int J = J0 + lane;
-    bool in = false, st = false;
-    if (J < nb) {
-        const float4 jl = __ldcg(&A.boxes[2 * (t0 + J)]), jh = __ldcg(&A.boxes[2 * (t0 + J) + 1]);
-        const float gx = fmaxf(0.0f, fmaxf(il.x - jh.x, jl.x - ih.x));
-        const float gy = fmaxf(0.0f, fmaxf(il.y - jh.y, jl.y - ih.y));
-        const float gz = fmaxf(0.0f, fmaxf(il.z - jh.z, jl.z - ih.z));
-        const float mx = fmaxf(ih.x - jl.x, jh.x - il.x);
-        const float my = fmaxf(ih.y - jl.y, jh.y - il.y);
-        const float mz = fmaxf(ih.z - jl.z, jh.z - il.z);
-        const float rmin2 = gx * gx + gy * gy + gz * gz;
-        const float rmax2 = mx * mx + my * my + mz * mz;
-        if (P::RADIUS_CUT) {
-            const float smax = fmaxf(ih.w, jh.w);
-            const float reach = A.rgbmax + smax, inner = A.rgbmax - smax;
-            in = rmin2 <= 1.001f * reach * reach;
-            st = inner <= 0.0f || rmax2 >= 0.999f * inner * inner;
-        } else {
-            in = rmin2 <= 1.001f * A.e_range2;
-            st = rmax2 >= 0.999f * A.cut2;
-        }
-    }
-    in_mask = __ballot_sync(0xffffffffu, in);
-    st_mask = __ballot_sync(0xffffffffu, st);
 }
 
 // Work of replica r is walked as super-rows K = 0 .. ceil(nb/2) - 1 (nb tiles
@@ -975,47 +970,32 @@ __device__ __forceinline__ void walk_task(const PairArgs& A, const int4 t, long 
     typename P::IState is;
     P::load_i(A, base, n, 64 * K, lane, is);
     const int next = (lane + 1) & 31;
-    // EF_CUT: straddling blocks run the pair code with EF_STRADDLE
+    // EF_CUT: straddling blocks run the pair code with EF_STRADDLE (the task
+    // list holds in-range blocks only, see k_block_list)
     constexpr int FS = (FLAGS & EF_CUT) ? (FLAGS | EF_STRADDLE) : FLAGS;
-    unsigned w_in = 0xffffffffu, w_st = 0u;
-    int w0 = -64;                              // first block of the cutoff window (none yet)
-    bool touched = !(FLAGS & EF_CUT);          // some block of this super-row ran (flush needed)
     for (int c = 0; c < cnt; ++c) {
-        bool run = true, straddle = false;
-        if (FLAGS & EF_CUT) {
-            if (J < w0 || J >= w0 + 32) {
-                cut_window<P>(A, r, K, J, nb, lane, w_in, w_st);
-                w0 = J;
-            }
-            run = (w_in >> (J - w0)) & 1u;
-            straddle = (w_st >> (J - w0)) & 1u;
+        const bool dx = (J == 2 * K);          // see run_tile: entry / exit rotation of a DX block
+        typename P::JState js;
+        P::load_j(A, base, n, 32 * J + ((lane + (dx ? 1 : 0)) & 31), js);
+        typename P::Part ip;
+        ip.zero();
+        const BlockInfo bi = block_info<P>(A, r, K, J, nb);
+        const bool straddle = (FLAGS & EF_CUT) && bi.straddle;
+        if (J >= 2 * K + 2) {
+            if (bi.far && !straddle) run_tile<P, FLAGS, M_FULL, true>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
+            else if (straddle) run_tile<P, FS, M_FULL, false>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
+            else run_tile<P, FLAGS, M_FULL, false>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
+        } else if (J == 2 * K) {
+            if (straddle) run_tile<P, FS, M_DX, false>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
+            else run_tile<P, FLAGS, M_DX, false>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
+        } else {
+            if (straddle) run_tile<P, FS, M_DY, false>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
+            else run_tile<P, FLAGS, M_DY, false>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
         }
-        if (run) {
-            const bool dx = (J == 2 * K);      // see run_tile: entry / exit rotation of a DX block
-            typename P::JState js;
-            P::load_j(A, base, n, 32 * J + ((lane + (dx ? 1 : 0)) & 31), js);
-            typename P::Part ip;
-            ip.zero();
-            const BlockInfo bi = block_info<P>(A, r, K, J, nb);
-            if (J >= 2 * K + 2) {
-                if (bi.far && !straddle) run_tile<P, FLAGS, M_FULL, true>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
-                else if (straddle) run_tile<P, FS, M_FULL, false>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
-                else run_tile<P, FLAGS, M_FULL, false>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
-            } else if (J == 2 * K) {
-                if (straddle) run_tile<P, FS, M_DX, false>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
-                else run_tile<P, FLAGS, M_DX, false>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
-            } else {
-                if (straddle) run_tile<P, FS, M_DY, false>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
-                else run_tile<P, FLAGS, M_DY, false>(A, is, js, ip, bi, 64 * K, 32 * J, lane, next);
-            }
-            P::fold_i(is, sa, lane, ip);
-            P::flush_j(A, base, n, 32 * J + ((lane + (dx ? 17 : 0)) & 31), js);
-            touched = true;
-        }
+        P::fold_i(is, sa, lane, ip);
+        P::flush_j(A, base, n, 32 * J + ((lane + (dx ? 17 : 0)) & 31), js);
         if (c + 1 < cnt && ++J == nb) {
-            w0 = -64;
-            if (touched) P::flush_i(A, r, base, n, 64 * K, lane, is, sa);
-            touched = !(FLAGS & EF_CUT);
+            P::flush_i(A, r, base, n, 64 * K, lane, is, sa);
 #pragma unroll
             for (int q = 0; q < 2 * P::NQ; ++q) sa[32 * q + lane] = 0;
             if (++K == nk) {
@@ -1032,7 +1012,7 @@ __device__ __forceinline__ void walk_task(const PairArgs& A, const int4 t, long 
             P::load_i(A, base, n, 64 * K, lane, is);
         }
     }
-    if (touched) P::flush_i(A, r, base, n, 64 * K, lane, is, sa);
+    P::flush_i(A, r, base, n, 64 * K, lane, is, sa);
 }
 
 
@@ -1048,6 +1028,27 @@ __global__ void __launch_bounds__(256, MINB) k_pairs(PairArgs A, const int4* __r
     const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (w >= n_tasks) return;
     walk_task<P, FLAGS>(A, tasks[w], s_acc + (threadIdx.x >> 5) * P::NQ * 64, lane);
+}
+
+// The same pass over a task list built on the device (cutoff passes: the
+// in-range blocks of k_block_list): the number of tasks is ctr[count_idx],
+// and warps take tasks one at a time from the queue head ctr[head_idx] until
+// it runs dry, so the grid only needs to fill the GPU.
+template <class P, int FLAGS, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_pairs_dyn(PairArgs A, const int4* __restrict__ tasks, int* ctr,
+                                                         int count_idx, int head_idx) {
+    pdl_enter();
+    extern __shared__ long long s_acc[];
+    const int lane = threadIdx.x & 31;
+    long long* sa = s_acc + (threadIdx.x >> 5) * P::NQ * 64;
+    const int n_tasks = __ldcg(&ctr[count_idx]);
+    for (;;) {
+        int w = 0;
+        if (lane == 0) w = atomicAdd(&ctr[head_idx], 1);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= n_tasks) break;
+        walk_task<P, FLAGS>(A, __ldcg(&tasks[w]), sa, lane);
+    }
 }
 
 // Launch of pass policy P over a task list; MAXCAP limits the register caps
