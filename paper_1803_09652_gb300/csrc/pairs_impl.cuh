@@ -210,20 +210,22 @@ __device__ __forceinline__ f2 hct_cut_fr2(f2 r, f2 rinv, f2 a, f2 s, float rc) {
 }
 
 // Disjoint spheres (r >= a + s) reaching past rc: the shells run from
-// L = r - s, and with u = t - L, w = min(rc - L, 2s), x = w / L the integral
-// takes a form without cancelling O(1/L) terms,
-//   H = 1/(4r) [ (2s/L) J1(x) - J2(x) ],
-//   J1 = x^2 / (2 (1+x)^2),   J2 = ln(1+x) - x (2 + 3x) / (2 (1+x)^2)
-// (J1 = int_0^x y/(1+y)^3 dy, J2 = int_0^x y^2/(1+y)^3 dy), w = 2s giving the
-// whole sphere.  w is formed as (rc - r) + s: rc - r is exact for the pairs
-// near the cutoff, so w carries one rounding.  Lanes with w <= 0 (sphere j
-// wholly past rc, masked lanes) give 0.
-__device__ __forceinline__ f2 log1pv(f2 x) { return make_float2(log1pf(x.x), log1pf(x.y)); }
+// L = r - s to U' = min(r + s, rc), and with w = U' - L, z = w / U' the
+// integral takes a form without cancelling O(1/L) terms,
+//   H = 1/(4r) [ (s/L) z^2 - J(z) ],   J(z) = -ln(1 - z) - z - z^2/2 = z^3 q(z)
+// (J = int_0^z t^2/(1-t) dt; q the fitted series of positive terms of
+// poly_coeffs.h: gb_poly_q for z <= 1/2, gb_poly_q_hi for z <= 3/4, which
+// covers every pair of disjoint spheres of the usual radius sets, and beyond
+// that J from the logarithm, where its terms cancel by less than a factor 10;
+// each range behind a warp vote over the lanes that use this form).  w is formed as
+// min((rc - r) + s, 2s): rc - r is exact for the pairs near the cutoff, so w
+// carries one rounding.  Lanes with w <= 0 (sphere j wholly past rc, masked
+// lanes) give 0.
 struct CutFar {
-    f2 x, iL, i1, J1, B;              // i1 = 1 / (1 + x)
-    bool cx, cy;                      // w = rc - L (the cutoff limits the shells)
+    f2 z, w, iL, iU, B;
+    bool cx, cy;                      // U' = rc (the cutoff limits the shells)
 };
-__device__ __forceinline__ CutFar hct_cut_far_terms(f2 r, f2 s, float rc) {
+__device__ __forceinline__ CutFar hct_cut_far_terms(f2 r, f2 s, float rc, bool use0 = true, bool use1 = true) {
     CutFar c;
     const f2 L = add2(r, neg2(s));
     c.iL = rcp2(L);
@@ -231,38 +233,46 @@ __device__ __forceinline__ CutFar hct_cut_far_terms(f2 r, f2 s, float rc) {
     const f2 s2 = add2(s, s);
     c.cx = wc.x < s2.x;
     c.cy = wc.y < s2.y;
-    const f2 w = make_float2(fmaxf(0.0f, c.cx ? wc.x : s2.x), fmaxf(0.0f, c.cy ? wc.y : s2.y));
-    c.x = mul2(w, c.iL);
-    c.i1 = rcp2(add2(F2(1.0f), c.x));
-    const f2 i12 = mul2(c.i1, c.i1);
-    c.J1 = mul2(mul2(F2(0.5f), mul2(c.x, c.x)), i12);
-    const f2 J2 = add2(log1pv(c.x), neg2(mul2(mul2(mul2(F2(0.5f), c.x), fma2(F2(3.0f), c.x, F2(2.0f))), i12)));
-    c.B = fma2(mul2(s2, c.iL), c.J1, neg2(J2));
+    c.w = make_float2(fmaxf(0.0f, c.cx ? wc.x : s2.x), fmaxf(0.0f, c.cy ? wc.y : s2.y));
+    const f2 U = add2(L, c.w);
+    c.iU = rcp2(U);
+    c.z = mul2(c.w, c.iU);
+    const f2 z2 = mul2(c.z, c.z), z3 = mul2(z2, c.z);
+    f2 J = mul2(z3, gb_poly_q2(c.z));
+    if (__any_sync(0xffffffffu, (use0 && c.z.x > GB_POLY_ZJ) || (use1 && c.z.y > GB_POLY_ZJ))) {
+        const f2 Jh = mul2(z3, gb_poly_q_hi2(add2(c.z, F2(-GB_POLY_ZMID))));
+        J = make_float2(c.z.x > GB_POLY_ZJ ? Jh.x : J.x, c.z.y > GB_POLY_ZJ ? Jh.y : J.y);
+        if (__any_sync(0xffffffffu, (use0 && c.z.x > GB_POLY_ZJ2) || (use1 && c.z.y > GB_POLY_ZJ2))) {
+            const f2 Jl = add2(logv(mul2(U, c.iL)), neg2(fma2(F2(0.5f), z2, c.z)));   // ln(U'/L) - z - z^2/2
+            J = make_float2(c.z.x > GB_POLY_ZJ2 ? Jl.x : J.x, c.z.y > GB_POLY_ZJ2 ? Jl.y : J.y);
+        }
+    }
+    c.B = fma2(mul2(s, c.iL), z2, neg2(J));
     return c;
 }
-__device__ __forceinline__ f2 hct_cut_far2(f2 r, f2 rinv, f2 s, float rc) {
-    return mul2(mul2(F2(0.25f), rinv), hct_cut_far_terms(r, s, rc).B);
+__device__ __forceinline__ f2 hct_cut_far2(f2 r, f2 rinv, f2 s, float rc, bool use0, bool use1) {
+    return mul2(mul2(F2(0.25f), rinv), hct_cut_far_terms(r, s, rc, use0, use1).B);
 }
-// -(dH/dr)/r of hct_cut_far2: with x' = -(1+x)/L while the cutoff limits the
-// shells and -x/L otherwise,
-//   dB/dr = -(2s/L^2) J1 + x' x (2s/L - x) / (1+x)^3,   dH/dr = (dB/dr - B/r) / (4r),
+// -(dH/dr)/r of hct_cut_far2: with z' = -1/U' while the cutoff limits the
+// shells and -z/U' otherwise (dJ/dz = z^2/(1-z), z/(1-z) = w/L),
+//   dB/dr = -(s/L^2) z^2 + z' z (2s - w) / L,   dH/dr = (dB/dr - B/r) / (4r),
 // where no two terms cancel.
-__device__ __forceinline__ f2 hct_cut_far_fr2(f2 r, f2 rinv, f2 s, float rc) {
-    const CutFar c = hct_cut_far_terms(r, s, rc);
-    const f2 s2 = add2(s, s);
-    const f2 i1 = c.i1;
-    const f2 xp = mul2(neg2(c.iL), make_float2(c.cx ? 1.0f + c.x.x : c.x.x, c.cy ? 1.0f + c.x.y : c.x.y));
-    const f2 t = mul2(mul2(mul2(xp, c.x), fma2(s2, c.iL, neg2(c.x))), mul2(mul2(i1, i1), i1));
-    const f2 dB = fma2(neg2(mul2(s2, mul2(c.iL, c.iL))), c.J1, t);
+__device__ __forceinline__ f2 hct_cut_far_fr2(f2 r, f2 rinv, f2 s, float rc, bool use0, bool use1) {
+    const CutFar c = hct_cut_far_terms(r, s, rc, use0, use1);
+    const f2 zp = neg2(make_float2(c.cx ? c.iU.x : c.z.x * c.iU.x, c.cy ? c.iU.y : c.z.y * c.iU.y));
+    const f2 t = mul2(mul2(zp, c.z), mul2(fma2(F2(2.0f), s, neg2(c.w)), c.iL));
+    const f2 dB = fma2(neg2(mul2(s, mul2(c.iL, c.iL))), mul2(c.z, c.z), t);
     const f2 dH = mul2(mul2(F2(0.25f), rinv), fma2(neg2(c.B), rinv, dB));
     return mul2(neg2(dH), rinv);
 }
-// One direction (descreened atom radius a, descreening sphere s) of a pair
-// that reaches past rc: the disjoint form where the spheres are apart, the
-// general restricted closed form (vote) where they overlap.
+// One direction (descreened atom radius a, descreening sphere s) of every
+// lane of a step in which some sphere crosses rc: disjoint spheres take the
+// restricted form above (the whole sphere while it lies inside the ball, 0
+// once it lies wholly past rc), overlapping ones the general restricted
+// closed form behind a vote.
 __device__ __forceinline__ f2 hct_cut_dir2(f2 r, f2 rinv, f2 a, f2 s, float rc) {
     const bool d0 = r.x >= a.x + s.x, d1 = r.y >= a.y + s.y;
-    f2 h = hct_cut_far2(r, rinv, s, rc);
+    f2 h = hct_cut_far2(r, rinv, s, rc, d0, d1);
     if (__any_sync(0xffffffffu, !(d0 && d1))) {
         const f2 g = hct_cut2(r, rinv, a, s, rc, 1.0f / rc);
         h = make_float2(d0 ? h.x : g.x, d1 ? h.y : g.y);
@@ -271,7 +281,7 @@ __device__ __forceinline__ f2 hct_cut_dir2(f2 r, f2 rinv, f2 a, f2 s, float rc) 
 }
 __device__ __forceinline__ f2 hct_cut_dir_fr2(f2 r, f2 rinv, f2 a, f2 s, float rc) {
     const bool d0 = r.x >= a.x + s.x, d1 = r.y >= a.y + s.y;
-    f2 h = hct_cut_far_fr2(r, rinv, s, rc);
+    f2 h = hct_cut_far_fr2(r, rinv, s, rc, d0, d1);
     if (__any_sync(0xffffffffu, !(d0 && d1))) {
         const f2 g = hct_cut_fr2(r, rinv, a, s, rc);
         h = make_float2(d0 ? h.x : g.x, d1 ? h.y : g.y);

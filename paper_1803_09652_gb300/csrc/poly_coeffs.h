@@ -30,3 +30,21 @@ __device__ __forceinline__ float gb_poly_hf(float y) {
 __device__ __forceinline__ float2 gb_poly_hf2(float2 y) {
     return __ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(make_float2(1.854454994e+01f, 1.854454994e+01f), y, make_float2(1.023153305e+01f, 1.023153305e+01f)), y, make_float2(8.925169945e+00f, 8.925169945e+00f)), y, make_float2(6.856277943e+00f, 6.856277943e+00f)), y, make_float2(4.800007343e+00f, 4.800007343e+00f)), y, make_float2(2.666666746e+00f, 2.666666746e+00f));
 }
+#define GB_POLY_ZJ 0.50000000f
+/* q(y) on [0, 0.5], degree 9, max relative error in FP32 Horner 1.19e-07 */
+__device__ __forceinline__ float gb_poly_q(float y) {
+    return fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(1.507509708e+00f, y, -2.156293154e+00f), y, 1.706731677e+00f), y, -5.312927365e-01f), y, 2.776696980e-01f), y, 1.213092506e-01f), y, 1.683840305e-01f), y, 1.999313831e-01f), y, 2.500010431e-01f), y, 3.333333433e-01f);
+}
+__device__ __forceinline__ float2 gb_poly_q2(float2 y) {
+    return __ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(make_float2(1.507509708e+00f, 1.507509708e+00f), y, make_float2(-2.156293154e+00f, -2.156293154e+00f)), y, make_float2(1.706731677e+00f, 1.706731677e+00f)), y, make_float2(-5.312927365e-01f, -5.312927365e-01f)), y, make_float2(2.776696980e-01f, 2.776696980e-01f)), y, make_float2(1.213092506e-01f, 1.213092506e-01f)), y, make_float2(1.683840305e-01f, 1.683840305e-01f)), y, make_float2(1.999313831e-01f, 1.999313831e-01f)), y, make_float2(2.500010431e-01f, 2.500010431e-01f)), y, make_float2(3.333333433e-01f, 3.333333433e-01f));
+}
+#define GB_POLY_ZJ2 0.75000000f
+#define GB_POLY_ZMID 0.62500000f
+/* q(z) on [0.5, 0.75] as a polynomial in y = z - 0.625: */
+/* q_hi(y) on [-0.125, 0.125], degree 8, max relative error in FP32 Horner 1.29e-07 */
+__device__ __forceinline__ float gb_poly_q_hi(float y) {
+    return fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(3.442066040e+02f, y, 1.440139923e+02f), y, 4.896784210e+01f), y, 2.128055954e+01f), y, 9.618304253e+00f), y, 4.423333168e+00f), y, 2.134392262e+00f), y, 1.110777140e+00f), y, 6.574766040e-01f);
+}
+__device__ __forceinline__ float2 gb_poly_q_hi2(float2 y) {
+    return __ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(make_float2(3.442066040e+02f, 3.442066040e+02f), y, make_float2(1.440139923e+02f, 1.440139923e+02f)), y, make_float2(4.896784210e+01f, 4.896784210e+01f)), y, make_float2(2.128055954e+01f, 2.128055954e+01f)), y, make_float2(9.618304253e+00f, 9.618304253e+00f)), y, make_float2(4.423333168e+00f, 4.423333168e+00f)), y, make_float2(2.134392262e+00f, 2.134392262e+00f)), y, make_float2(1.110777140e+00f, 1.110777140e+00f)), y, make_float2(6.574766040e-01f, 6.574766040e-01f));
+}

@@ -1,10 +1,11 @@
 """GPU GB with cutoffs (gb_params.rgbmax, gb_params.cut) against the FP64
 oracle with the same cutoffs: Born radii, energies, forces and dE/dq element
 by element on ragged batches (cutoffs from below a contact distance to past
-the molecule), the Monte Carlo energy change, one MD step, the allocation-free
-entry point, cutoffs past the molecule bitwise equal to none, and the block
-skip (a cut evaluation of a 100000-atom chain runs in a fraction of the time
-of the full one, with sampled radii and the zero net force still right)."""
+the molecule; batches with empty replicas), the Monte Carlo energy change and
+the per-residue sweep, one MD step, the allocation-free entry point, cutoffs
+past the molecule bitwise equal to none, and the block neighbour list (a cut
+evaluation of a 100000-atom chain runs in a fraction of the time of the full
+one, with sampled radii and the zero net force still right)."""
 import ctypes as C
 import time
 
@@ -79,6 +80,58 @@ def test_cutoff_energy_forces_match_oracle(pkg, rgbmax, cut, kappa):
     p = oracle_params(rgbmax=f32(rgbmax), cut=f32(cut), kappa=f32(kappa))
     ref = oracle.batch_energy_forces(b, p, with_phi=True)
     _check(out, ref, born_bar(b, p))
+
+
+def test_cutoff_batch_with_empty_replicas(pkg):
+    """Empty replicas before, between and after the others: the list builder's
+    replica search and the lists' runs stay inside each replica."""
+    b = synth.random_batch([0, 700, 0, 33, 1, 1200, 0], seed=47)
+    out = _run(pkg, b, rgbmax=8.0, cut=9.0)
+    p = oracle_params(rgbmax=8.0, cut=9.0)
+    ref = oracle.batch_energy_forces(b, p, with_phi=True)
+    _check(out, ref, born_bar(b, p))
+
+
+def test_cutoff_sweep_matches_oracle(pkg):
+    """Per-residue sweeps (every site of a kind in random order) with the pair
+    cutoff in the site rows and the site-site block."""
+    import torch
+    dev = device()
+    rgbmax, cut = 10.0, 7.0
+    p = oracle_params(rgbmax=f32(rgbmax), cut=f32(cut))
+    reps = [synth.make_replica(n, 90 + k, specs) for k, (n, specs) in enumerate([
+        (400, [(1, 8, 2), (0, 6, 4), (0, 9, 3), (0, 5, 2), (1, 12, 2)]),
+        (150, [(0, 12, 3), (1, 6, 2)]),
+    ])]
+    b = synth.Batch(reps, pH=np.array([4.4, 4.9]), E=synth.E0_REF_V + np.array([0.0, 0.03]))
+    G = np.concatenate([oracle.site_reference_energies(synth.Batch([r], pH=b.pH[k:k + 1], E=b.E[k:k + 1]), p)
+                        for k, r in enumerate(b.replicas)])
+    t = b.site_tables(G)
+    xyzq, rad = to_dev(b, dev)
+    ctx = pkg.Context(b.atom_off, pkg.default_params(rgbmax=rgbmax, cut=cut))
+    R = ctx.born_radii(xyzq, rad)
+    sites = pkg.SiteTables(t, b.n_rep, dev)
+    state = torch.zeros(t["n_sites"], dtype=torch.int32, device=dev)
+    pH, E = torch.as_tensor(b.pH, device=dev), torch.as_tensor(b.E, device=dev)
+    x, q, rho, scr, off = oracle.batch_arrays(b)
+    q = q.copy()
+    st = b.initial_states()
+    Rn = R.double().cpu().numpy()
+    for step in range(10):
+        for kind in (0, 1):
+            dG, acc = ctx.mc_sweep(sites, xyzq, R, pH, E, KT, 13, step, kind, state)
+            o = oracle.mc_sweep(off, x, q, Rn, t, st, b.pH, b.E, KT, 13, step, kind, p)
+            dG, acc = dG.cpu().numpy(), acc.cpu().numpy()
+            vis = o["visit"] >= 0
+            assert np.all(np.abs(dG[vis] - o["dG"][vis]) <= DG_ABS), (step, kind)
+            diff = np.flatnonzero(acc[vis] != o["acc"][vis])
+            for s_ in np.flatnonzero(vis)[diff]:
+                assert abs(o["dG"][s_] - o["thresh"][s_]) <= DG_ABS
+            if diff.size:
+                state.copy_(torch.as_tensor(st, device=dev))
+                xyzq[:, 3] = torch.as_tensor(q, dtype=torch.float32, device=dev)
+            assert np.array_equal(state.cpu().numpy(), st)
+    ctx.sync_status()
 
 
 def test_cutoffs_past_the_molecule_are_the_uncut_path(pkg):
