@@ -130,13 +130,13 @@ def q2_fit():
     raise RuntimeError("no fit")
 
 
-def main():
+def main(out=None):
     full = best_fits(Y_MAX)
     far = best_fits(Y_FAR)
     qdeg, qc, qerr = q_fit()
     q2deg, q2c, q2err, z0 = q2_fit()
     here = os.path.dirname(os.path.abspath(__file__))
-    with open(os.path.join(here, "poly_coeffs.h"), "w") as fh:
+    with open(out or os.path.join(here, "poly_coeffs.h"), "w") as fh:
         fh.write("/* Generated by gen_poly.py: far-field HCT polynomials, see that script. */\n")
         fh.write("#pragma once\n")
         fh.write(f"#define GB_POLY_YMAX {Y_MAX:.8f}f\n")
