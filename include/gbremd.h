@@ -289,7 +289,9 @@ typedef struct {
 /* Advance the batch by nsteps MD steps.  Step t (1-based, absolute) is
  * followed by MC attempts when t % mc_every == 0 and by an exchange when
  * t % ex_every == 0.  Requires state->force to hold the forces at the
- * incoming coordinates (gb_md_init computes them). */
+ * incoming coordinates (gb_md_init computes them).  gb_md_init is also the
+ * restart point after a device error: it clears the context's accumulators
+ * before it evaluates. */
 int gb_md_init(gb_ctx* ctx, gb_md_state* state, void* stream);
 int gb_md_segment(gb_ctx* ctx, gb_md_state* state, const gb_sites* sites, int64_t nsteps,
                   void* stream);
@@ -344,6 +346,13 @@ int gb_pass_times(gb_ctx* ctx, double* mean_ms);
  * out[0] the mean ms per MD step inside the persistent launches of the last
  * block, out[1] the mean ms per launch and out[2] the mean steps per launch. */
 int gb_set_persistent(gb_ctx* ctx, int32_t enable);
+/* Bound of every dependency wait inside the persistent MD kernel, in polls of
+ * about 64 ns (0 restores the default 2^22, about a quarter of a second).  A
+ * wait that runs out records GB_ERR_TIMEOUT in the context's error word
+ * (gb_sync_status); the other warps then stop too and the launch ends, with
+ * the MD state of that segment left undefined and the context usable (call
+ * gb_md_init again).  GB_ERR_INVALID_ARG for a negative or too large value. */
+int gb_set_wait_limit(gb_ctx* ctx, int64_t polls);
 int gb_persist_times(gb_ctx* ctx, double* out);
 
 #ifdef __cplusplus

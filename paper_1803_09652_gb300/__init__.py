@@ -118,6 +118,7 @@ def load(path: Optional[str] = None):
         "gb_set_profiling": [_P, i32],
         "gb_pass_times": [_P, C.POINTER(C.c_double)],
         "gb_set_persistent": [_P, i32],
+        "gb_set_wait_limit": [_P, C.c_int64],
         "gb_persist_times": [_P, C.POINTER(C.c_double)],
     }
     for name, args in sig.items():
@@ -317,6 +318,10 @@ class Context:
 
     def set_persistent(self, on: bool):
         _check(self.lib.gb_set_persistent(self.h, 1 if on else 0), self.h)
+
+    def set_wait_limit(self, polls: int):
+        """Polls before a persistent-kernel dependency wait gives up (0: default)."""
+        _check(self.lib.gb_set_wait_limit(self.h, int(polls)), self.h)
 
     def persist_times(self):
         """(ms per MD step, ms per launch, steps per launch) of the persistent

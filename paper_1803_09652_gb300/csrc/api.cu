@@ -62,6 +62,7 @@ struct gb_ctx {
     int* phase_count = nullptr;         // [6][M]
     int phase_base[7] = {0};
     unsigned* qwords = nullptr;         // queue head + 6 x M completion counters
+    unsigned spin_limit = 1u << 22;     // polls before a persistent-kernel wait gives up
     std::vector<int> prof_steps_per_launch;
     // cached MD graph
     cudaGraphExec_t md_exec = nullptr;
@@ -252,6 +253,7 @@ gbk::PairArgs pair_args(const gb_ctx* c, const float* xyzq, const float* rad) {
     a.N = c->N;
     a.boxes = c->boxes;
     a.tile_off = c->tile_off;
+    a.err = c->err;
     return a;
 }
 
@@ -845,6 +847,7 @@ int enqueue_steps(gb_ctx* c, gb_md_state* st, const gb_sites* sites, int64_t len
         a.head = c->qwords;
         a.done = c->qwords + 1;
         a.err = c->err;
+        a.spin_limit = c->spin_limit;
         if (c->prof) {
             int rc = ensure_prof_events(c, len);
             if (rc) return rc;
@@ -921,6 +924,15 @@ extern "C" int gb_md_init(gb_ctx* c, gb_md_state* st, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     const int flags = (c->p.rep_k != 0.0f) ? gbk::EF_REP : 0;
     const gbk::MDArgs m = md_args(c, st);
+    // a restart point: a segment that stopped early (a wait that ran out) may
+    // have left partial sums in the accumulators, which the kernels otherwise
+    // clear as they read them
+    const size_t N = (size_t)c->N;
+    GB_CHECK(c, cudaMemsetAsync(c->I_acc, 0, sizeof(u64) * N, s));
+    GB_CHECK(c, cudaMemsetAsync(c->dR_acc, 0, sizeof(u64) * N, s));
+    GB_CHECK(c, cudaMemsetAsync(c->phi_acc, 0, sizeof(u64) * N, s));
+    GB_CHECK(c, cudaMemsetAsync(c->F_acc, 0, sizeof(u64) * 3 * N, s));
+    GB_CHECK(c, cudaMemsetAsync(c->E_acc, 0, sizeof(u64) * 4 * (size_t)c->M, s));
     rc = evaluate(c, st->xyzq, st->rad_screen, st->R, flags, nullptr, s, nullptr, &m, true);
     if (rc) return rc;
     GB_CHECK(c, gbk::launch_md_step(atom_args(c, st->xyzq, st->rad_screen), m, nullptr, nullptr, 0, gbk::MD_CLOSE, s));
@@ -1105,6 +1117,15 @@ extern "C" int gb_pass_times(gb_ctx* c, double* mean_ms) {
 extern "C" int gb_set_persistent(gb_ctx* c, int32_t enable) {
     if (!c) return fail(nullptr, GB_ERR_INVALID_ARG, "NULL context");
     c->use_persist = enable != 0;
+    if (c->md_exec) { cudaGraphExecDestroy(c->md_exec); c->md_exec = nullptr; c->md_key.clear(); }
+    return GB_OK;
+}
+
+extern "C" int gb_set_wait_limit(gb_ctx* c, int64_t polls) {
+    if (!c) return fail(nullptr, GB_ERR_INVALID_ARG, "NULL context");
+    if (polls < 0 || polls > 0xffffffffLL) return fail(c, GB_ERR_INVALID_ARG, "polls must be 0 .. 2^32 - 1");
+    c->spin_limit = polls == 0 ? (1u << 22) : (unsigned)polls;
+    // captured launches carry the limit: rebuild the MD graph on next use
     if (c->md_exec) { cudaGraphExecDestroy(c->md_exec); c->md_exec = nullptr; c->md_key.clear(); }
     return GB_OK;
 }

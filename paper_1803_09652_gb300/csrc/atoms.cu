@@ -147,7 +147,7 @@ __global__ void k_md_step(AtomArgs A, MDArgs m, float4* boxes, const int* tile_o
                 a = rs.x - A.offset;
                 sc = rs.y * a;
             }
-            tile_box_store(boxes, (int64_t)tile_off[r] + t, valid, x.x, x.y, x.z, a, sc);
+            tile_box_store(boxes, (int64_t)tile_off[r] + t, valid, x.x, x.y, x.z, a, sc, x.w, A.err);
         }
     }
 }

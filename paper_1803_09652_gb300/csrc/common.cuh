@@ -44,8 +44,13 @@ __device__ __forceinline__ float shfl(float v, int src) { return __shfl_sync(0xf
 // it; lanes without an atom pass valid = false): lo.xyz with the largest
 // a = rho - offset, hi.xyz with the largest screened radius s, stored by
 // lane 0 at boxes[2t], boxes[2t + 1].
+// Also the finiteness check of the evaluation's input: a lane whose atom has a
+// non-finite coordinate or charge records GB_ERR_NONFINITE (err nullable; the
+// int64 fixed-point sums would otherwise turn NaN into a silent zero).
 __device__ __forceinline__ void tile_box_store(float4* boxes, int64_t t, bool valid, float x, float y, float z,
-                                               float a, float s) {
+                                               float a, float s, float q, int* err) {
+    if (valid && err && !(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(q)))
+        atomicCAS(err, 0, GB_ERR_NONFINITE);
     float x0 = valid ? x : INFINITY, y0 = valid ? y : INFINITY, z0 = valid ? z : INFINITY;
     float x1 = valid ? x : -INFINITY, y1 = valid ? y : -INFINITY, z1 = valid ? z : -INFINITY;
     float am = valid ? a : 0.0f, sm = valid ? s : 0.0f;

@@ -33,6 +33,7 @@ struct PairArgs {
     int64_t N;
     float4* boxes;             // [2 * tiles] bounding boxes of 32-atom tiles (nullable)
     const int* tile_off;       // [M+1] first tile of each replica
+    int* err;                  // device error word (non-finite input, nullable)
 };
 
 // One warp task: replica, super-row K (atoms 64K .. 64K+63), first tile J
@@ -252,6 +253,7 @@ struct PersistArgs {
     unsigned* head;            // queue head, followed by the 6 x M completion counters
     unsigned* done;
     int* err;
+    unsigned spin_limit;       // polls before a dependency wait gives up (GB_ERR_TIMEOUT)
 };
 size_t persist_smem();
 cudaError_t persist_occupancy(int rep, int* blocks_per_sm);

@@ -1089,15 +1089,15 @@ __device__ __forceinline__ void tile_box_warp(const PairArgs& A, int M, int t, i
     const int64_t base = A.atom_off[r];
     const int n = (int)(A.atom_off[r + 1] - base);
     const int i = 32 * (t - A.tile_off[r]) + lane;
-    float x = 0.0f, y = 0.0f, z = 0.0f, am = 0.0f, sm = 0.0f;
+    float x = 0.0f, y = 0.0f, z = 0.0f, q = 0.0f, am = 0.0f, sm = 0.0f;
     if (i < n) {
         const float4 p = __ldcg(&A.xyzq[base + i]);
         const float2 rs = A.rad[base + i];
-        x = p.x; y = p.y; z = p.z;
+        x = p.x; y = p.y; z = p.z; q = p.w;
         am = rs.x - A.offset;
         sm = rs.y * am;
     }
-    tile_box_store(A.boxes, t, i < n, x, y, z, am, sm);
+    tile_box_store(A.boxes, t, i < n, x, y, z, am, sm, q, A.err);
 }
 
 

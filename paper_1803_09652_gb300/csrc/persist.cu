@@ -21,14 +21,15 @@
 // still finishing, other warps already work on the next pass of the first
 // replicas: the pass tails of a small batch overlap.
 //
-// Waits are bounded: after SPIN_LIMIT polls the warp records GB_ERR_TIMEOUT and
-// stops taking work; the others then time out on it and stop too.
+// Waits are bounded: after P.spin_limit polls (2^22 by default, about a
+// quarter of a second; gb_set_wait_limit) the warp records GB_ERR_TIMEOUT and
+// stops taking work; the others then see the error word, or time out on it,
+// and stop too, so the launch always ends and the context stays usable.
 #include "atoms_impl.cuh"
 #include "pairs_impl.cuh"
 
 namespace gbk {
 
-constexpr unsigned SPIN_LIMIT = 1u << 22;
 constexpr int PERSIST_THREADS = 128;
 constexpr int PERSIST_NQ = Energy::NQ;   // largest i-side accumulator slot of the three passes
 
@@ -40,13 +41,14 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 
 // Lane 0 waits until *ctr >= target; returns false when the wait gave up or
 // another warp reported an error.
-__device__ __forceinline__ bool wait_count(const unsigned* ctr, unsigned target, int* err, int lane) {
+__device__ __forceinline__ bool wait_count(const unsigned* ctr, unsigned target, int* err, unsigned limit,
+                                           int lane) {
     int ok = 1;
     if (lane == 0) {
         unsigned it = 0;
         while (ld_acquire(ctr) < target) {
             if (*(volatile int*)err != 0) { ok = 0; break; }
-            if (++it > SPIN_LIMIT) {
+            if (++it > limit) {
                 atomicCAS(err, 0, GB_ERR_TIMEOUT);
                 ok = 0;
                 break;
@@ -144,9 +146,10 @@ __global__ void __launch_bounds__(PERSIST_THREADS, 6) k_md_persist(PersistArgs P
         bool ok = true;
         if (p > 0) {
             ok = wait_count(&P.done[(p - 1) * P.M + r], (unsigned)(s + 1) * (unsigned)P.count[(p - 1) * P.M + r],
-                            P.err, lane);
+                            P.err, P.spin_limit, lane);
         } else if (s > 0) {
-            ok = wait_count(&P.done[5 * P.M + r], (unsigned)s * (unsigned)P.count[5 * P.M + r], P.err, lane);
+            ok = wait_count(&P.done[5 * P.M + r], (unsigned)s * (unsigned)P.count[5 * P.M + r], P.err,
+                            P.spin_limit, lane);
         }
         if (!ok) break;
         switch (p) {

@@ -138,3 +138,54 @@ def test_persistent_driver_tracks_three_pass_driver(pkg):
     c2.sync_status()
     d = (S1["xyzq"] - S2["xyzq"]).abs().max().item()
     assert d < 1e-3, d
+
+
+def test_persistent_wait_that_runs_out_reports_a_timeout(pkg):
+    """A dependency wait of the persistent kernel limited to one poll runs out
+    (the phases of a 2048-atom replica take microseconds): the launch ends,
+    gb_sync_status reports GB_ERR_TIMEOUT, and after the default limit is
+    restored the same context runs the same segment to the same result as the
+    multi-launch path."""
+    import torch
+    b = synth.random_batch([2048, 1500], seed=21, sites=False)
+    ctx, st, S, _ = _setup(pkg, b, seed=8, persistent=True)
+    x0 = S["xyzq"].clone()
+    ctx.set_wait_limit(1)
+    ctx.md_segment(st, None, 4)
+    torch.cuda.synchronize()
+    with pytest.raises(RuntimeError, match="TIMEOUT"):
+        ctx.sync_status()
+    ctx.set_wait_limit(0)
+    S["xyzq"].copy_(x0)
+    S["vel"].zero_()
+    st.step, st.attempt = 0, 0
+    ctx.md_init(st)
+    ctx.md_segment(st, None, 4)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    ref, st2, S2, _ = _setup(pkg, b, seed=8, persistent=False)
+    ref.md_segment(st2, None, 4)
+    torch.cuda.synchronize()
+    ref.sync_status()
+    assert torch.equal(S["xyzq"], S2["xyzq"]) and torch.equal(S["vel"], S2["vel"])
+
+
+def test_non_finite_coordinates_are_reported(pkg):
+    """A NaN coordinate gives a non-finite Born radius: the evaluation records
+    GB_ERR_NONFINITE, and the context evaluates valid input afterwards."""
+    import torch
+    dev = device()
+    b = synth.random_batch([300, 64], seed=22, sites=False)
+    ctx = pkg.Context(b.atom_off)
+    xyzq = torch.as_tensor(b.xyzq(), device=dev)
+    rad = torch.as_tensor(b.rad_screen(), device=dev)
+    bad = xyzq.clone()
+    bad[17, 0] = float("nan")
+    ctx.energy_forces(bad, rad)
+    torch.cuda.synchronize()
+    with pytest.raises(RuntimeError, match="NONFINITE"):
+        ctx.sync_status()
+    out = ctx.energy_forces(xyzq, rad)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    assert torch.isfinite(out["F"]).all() and torch.isfinite(out["E"]).all()
