@@ -449,6 +449,11 @@ struct Born {
         j.x = shfl(j.x, src); j.y = shfl(j.y, src); j.z = shfl(j.z, src);
         j.a = shfl(j.a, src); j.s = shfl(j.s, src);
     }
+    // far blocks never read a: it is left behind (the block reloads it)
+    static __device__ __forceinline__ void rotate_far(JState& j, int src) {
+        j.x = shfl(j.x, src); j.y = shfl(j.y, src); j.z = shfl(j.z, src);
+        j.s = shfl(j.s, src);
+    }
     static __device__ __forceinline__ void rotate_acc(JState& j, int src) { j.acc = shfl(j.acc, src); }
     static __device__ __forceinline__ void take_data(JState& j, const JState& d) {
         j.x = d.x; j.y = d.y; j.z = d.z; j.a = d.a; j.s = d.s;
@@ -603,6 +608,7 @@ struct Energy {
         j.x = shfl(j.x, src); j.y = shfl(j.y, src); j.z = shfl(j.z, src);
         j.q = shfl(j.q, src); j.R = shfl(j.R, src); j.h = shfl(j.h, src);
     }
+    static __device__ __forceinline__ void rotate_far(JState& j, int src) { rotate_data(j, src); }
     template <int FLAGS>
     static __device__ __forceinline__ void rotate_acc_f(JState& j, int src) {
         j.fx = shfl(j.fx, src); j.fy = shfl(j.fy, src); j.fz = shfl(j.fz, src);
@@ -782,6 +788,10 @@ struct Chain {
         j.x = shfl(j.x, src); j.y = shfl(j.y, src); j.z = shfl(j.z, src);
         j.a = shfl(j.a, src); j.s = shfl(j.s, src); j.c = shfl(j.c, src);
     }
+    static __device__ __forceinline__ void rotate_far(JState& j, int src) {
+        j.x = shfl(j.x, src); j.y = shfl(j.y, src); j.z = shfl(j.z, src);
+        j.s = shfl(j.s, src); j.c = shfl(j.c, src);
+    }
     static __device__ __forceinline__ void rotate_acc(JState& j, int src) {
         j.fx = shfl(j.fx, src); j.fy = shfl(j.fy, src); j.fz = shfl(j.fz, src);
     }
@@ -848,7 +858,8 @@ __device__ __forceinline__ void run_tile(const PairArgs& A, const typename P::IS
         // the next step's j data are fetched before this step's arithmetic, so
         // that only the short accumulator chain is serial between steps
         typename P::JState nx = js;
-        P::rotate_data(nx, next);
+        if (FAR) P::rotate_far(nx, next);
+        else P::rotate_data(nx, next);
         const Mask m = step_mask<MODE>(k, lane);
         bool busy = true;
         if (FLAGS & EF_STRADDLE) {   // every pair of this step wholly past the cutoff's reach
