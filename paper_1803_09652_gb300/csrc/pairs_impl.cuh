@@ -181,7 +181,9 @@ __device__ __forceinline__ f2 hct_cut2(f2 r, f2 rinv, f2 a, f2 s, float rc, floa
 //   dB/dr = -dL/L^2 + dU/U'^2 + (1 + s^2/r^2)/4 (1/U'^2 - 1/L^2)
 //           + w/2 (dL/L^3 - dU/U'^3) - ln(L/U') / (2 r^2) + (dL/L - dU/U') / (2r)
 // (0 when L >= U'), plus 2 dL/L^2 when engulfed with L < rc.
-__device__ __forceinline__ f2 hct_cut_fr2(f2 r, f2 rinv, f2 a, f2 s, float rc) {
+// (out of line: the chain pass's straddle code would not fit the instruction
+// cache with it inlined into every block mode)
+static __device__ __noinline__ f2 hct_cut_fr2(f2 r, f2 rinv, f2 a, f2 s, float rc) {
     const f2 U = add2(r, s);
     const bool cx = U.x > rc, cy = U.y > rc;
     const f2 Up = make_float2(cx ? rc : U.x, cy ? rc : U.y);
@@ -853,7 +855,10 @@ __device__ __forceinline__ void run_tile(const PairArgs& A, const typename P::IS
     // a DX block pairs the x half with its own tile: only steps 1 .. 16 carry
     // pairs (js enters rotated by one and leaves rotated by 17)
     constexpr int K0 = (MODE == M_DX) ? 1 : 0, K1 = (MODE == M_DX) ? 17 : 32;
-#pragma unroll P::UNROLL
+    // straddling blocks carry the long restricted-integral code: not unrolled,
+    // so that it fits the instruction cache
+    constexpr int U = (FLAGS & EF_STRADDLE) ? 1 : P::UNROLL;
+#pragma unroll U
     for (int k = K0; k < K1; ++k) {
         // the next step's j data are fetched before this step's arithmetic, so
         // that only the short accumulator chain is serial between steps
