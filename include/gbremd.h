@@ -110,8 +110,9 @@ int gb_set_tiles(gb_ctx* ctx, int32_t warps_per_block, int32_t tiles_per_task);
 /* Register cap of the pair kernel of one pass (0 Born radii, 1 energy and
  * direct forces, 2 Born chain rule; -1 = all three), as 256-thread blocks
  * per SM: 1 = the compiler's choice, 3 = at most 80 registers per thread,
- * 4 = at most 64 (more resident warps, more spills).  gb_autotune picks
- * each pass's cap; the default is 3.  GB_ERR_INVALID_ARG for other values. */
+ * 4 = at most 64 (more resident warps, more spills; a pass with a cutoff
+ * runs cap 3 instead).  gb_autotune picks each pass's cap; the default is 3.
+ * GB_ERR_INVALID_ARG for other values. */
 int gb_set_reg_cap(gb_ctx* ctx, int32_t pass, int32_t min_blocks_per_sm);
 /* The three caps in pass order into caps[3] (host memory). */
 int gb_get_reg_caps(const gb_ctx* ctx, int32_t* caps);

@@ -12,7 +12,8 @@
 // the warps' work evens out whatever the list's order.
 //
 // Counters (one int each): [0] Born-list length, [1] energy-list length,
-// [2] [3] [4] queue heads of the Born, energy and chain passes.
+// [2] [3] [4] queue heads of the Born, energy and chain passes.  The cutoff
+// kernels come with register caps 1 and 3 (a request for 4 takes 3).
 #include "pairs_impl.cuh"
 
 namespace gbk {
@@ -78,31 +79,41 @@ __global__ void k_block_list(PairArgs A, const int* __restrict__ win_off, int M,
     if (want_e) emit_runs(__ballot_sync(0xffffffffu, in_e), lane, r, K, J0, list_e, &ctr[1]);
 }
 
+constexpr int MAX_DEVICES = 64;
+
+int current_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) dev = 0;
+    return dev;
+}
+
+// Resident blocks per SM of one instantiation at wpb warps per block, cached
+// per device (0 = not queried yet; a lost race only repeats the query).
 template <class P, int FLAGS, int MINB>
 int resident_blocks(int wpb) {
-    // per (instantiation, warps per block); 0 = not queried yet
-    static int cache[17] = {0};
+    static int cache[MAX_DEVICES][17] = {};
     if (wpb < 1 || wpb > 16) return 1;
-    if (!cache[wpb]) {
+    int& c = cache[current_device()][wpb];
+    if (!c) {
         int per_sm = 0;
         const size_t smem = (size_t)wpb * P::NQ * 64 * sizeof(long long);
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs_dyn<P, FLAGS, MINB>, 32 * wpb, smem) !=
                 cudaSuccess || per_sm < 1)
             per_sm = 1;
-        cache[wpb] = per_sm;
+        c = per_sm;
     }
-    return cache[wpb];
+    return c;
 }
 
 int sm_count() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
-            sms = 1;
+    static int cache[MAX_DEVICES] = {};
+    const int dev = current_device();
+    if (!cache[dev]) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+        cache[dev] = sms;
     }
-    return sms;
+    return cache[dev];
 }
 
 template <class P, int FLAGS, int MINB>
