@@ -335,6 +335,81 @@ class Context:
         _check(self.lib.gb_md_segment(self.h, C.byref(st), sp, int(nsteps), _stream(stream)), self.h)
 
 
+class Simulation:
+    """Batched C(pH,E)-REMD MD driver: the device state of a batch and the
+    gb_md_state that points at it.  run(n) advances n BAOAB MD steps, with the
+    Monte Carlo attempts and exchanges they contain, through gb_md_segment
+    (one captured graph per block of steps).
+
+    xyzq float32 [N, 4] (x, y, z, q) and rad_screen float32 [N, 2] (rho, S)
+    are copied to the device.  sites: a site table dict (the layout
+    SiteTables takes) or None.  pH, E: float64 [M] per replica.  E_ladder,
+    pH_ladder: the exchange grid's ladders, replica p * n_E + e starting at pH
+    row p and E column e; exchanges run when n_E * n_pH == M > 1, along E
+    (ex_dim 0), pH (1) or alternating (2, the default on a 2-D grid).
+    Attributes xyzq, vel, force, R, state, pH, E, grid are the live device
+    tensors."""
+
+    def __init__(self, atom_off, xyzq, rad_screen, params: Optional[Params] = None, sites=None, pH=None,
+                 E=None, E_ladder=None, pH_ladder=None, *, dt=0.002, friction=10.0, mass=12.0,
+                 temperature=300.0, bond_k=300.0, bond_r0=1.5, seed=0, mc_every=10, ex_every=100,
+                 ex_dim=None, wrap=True, mc_mode=0, device=0):
+        import torch
+        dev = torch.device("cuda", device)
+        self.ctx = Context(atom_off, params, device)
+        M, N = self.ctx.M, self.ctx.N
+        f32 = dict(dtype=torch.float32, device=dev)
+        f64 = dict(dtype=torch.float64, device=dev)
+        self.xyzq = torch.as_tensor(xyzq, **f32).reshape(N, 4).clone()
+        self.rad = torch.as_tensor(rad_screen, **f32).reshape(N, 2).clone()
+        self.vel = torch.zeros((N, 4), **f32)
+        self.force = torch.zeros((N, 4), **f32)
+        self.R = torch.zeros(N, **f32)
+        self.pH = torch.as_tensor(np.full(M, 7.0) if pH is None else pH, **f64).clone()
+        self.E = torch.as_tensor(np.zeros(M) if E is None else E, **f64).clone()
+        E_lad = np.asarray(self.E.cpu().numpy()[:1] if E_ladder is None else E_ladder, np.float64)
+        pH_lad = np.asarray(self.pH.cpu().numpy()[:1] if pH_ladder is None else pH_ladder, np.float64)
+        self.E_ladder = torch.as_tensor(E_lad, **f64)
+        self.pH_ladder = torch.as_tensor(pH_lad, **f64)
+        self.grid = torch.arange(M, dtype=torch.int32, device=dev)
+        self.sites = SiteTables(sites, M, dev) if sites is not None else None
+        n_sites = int(sites["n_sites"]) if sites is not None else 0
+        self.state = torch.zeros(max(n_sites, 1), dtype=torch.int32, device=dev)
+        n_E, n_pH = len(E_lad), len(pH_lad)
+        ladder = n_E * n_pH == M and M > 1
+        st = MDState()
+        st.xyzq, st.vel, st.force = self.xyzq.data_ptr(), self.vel.data_ptr(), self.force.data_ptr()
+        st.rad_screen, st.R = self.rad.data_ptr(), self.R.data_ptr()
+        st.state, st.pH, st.E = self.state.data_ptr(), self.pH.data_ptr(), self.E.data_ptr()
+        st.grid, st.E_ladder, st.pH_ladder = self.grid.data_ptr(), self.E_ladder.data_ptr(), self.pH_ladder.data_ptr()
+        st.n_E, st.n_pH = (n_E, n_pH) if ladder else (M, 1)
+        st.dt, st.friction, st.mass, st.kT = dt, friction, mass, KB * temperature
+        st.bond_k, st.bond_r0 = bond_k, bond_r0
+        st.seed, st.step, st.attempt = seed, 0, 0
+        st.mc_every = mc_every if self.sites is not None else 0
+        st.ex_every = ex_every if (ladder and self.sites is not None) else 0
+        st.ex_dim = (2 if n_pH > 1 else 0) if ex_dim is None else ex_dim
+        st.wrap, st.mc_mode = 1 if wrap else 0, mc_mode
+        self.st = st
+        self.ctx.md_init(st)
+
+    @property
+    def step(self) -> int:
+        return int(self.st.step)
+
+    def run(self, nsteps: int, stream=None) -> "Simulation":
+        self.ctx.md_segment(self.st, self.sites, int(nsteps), stream)
+        return self
+
+    def sync(self, stream=None):
+        """Waits for the work enqueued so far; raises on a recorded device error."""
+        self.ctx.sync_status(stream)
+
+    def energies(self):
+        """[M, 3] float64 (GB, Coulomb, soft repulsion) at the current coordinates."""
+        return self.ctx.energy_forces(self.xyzq, self.rad, want=("E",))["E"]
+
+
 def eremd_exchange(values, rep_at_slot, n_count, dim, attempt, seed, kT, wrap=True,
                    n_ladders=1, ladder_len=None, ladder_stride=None, slot_stride=1,
                    value_of_rep=None, delta_out=None, acc_out=None, stream=None):

@@ -189,3 +189,26 @@ def test_non_finite_coordinates_are_reported(pkg):
     torch.cuda.synchronize()
     ctx.sync_status()
     assert torch.isfinite(out["F"]).all() and torch.isfinite(out["E"]).all()
+
+
+def test_simulation_driver_equals_the_state_struct_path(pkg):
+    """pkg.Simulation (the Python driver) runs the same MD, MC and exchanges as
+    a gb_md_state filled by hand: identical coordinates, site states and
+    exchange grid after 60 steps."""
+    import torch
+    b = synth.config_eremd(4, 300)
+    t = b.site_tables(oracle.site_reference_energies(b, oracle_params()))
+    sim = pkg.Simulation(b.atom_off, b.xyzq(), b.rad_screen(), pkg.default_params(rep_k=10.0, rep_sigma=2.5),
+                         sites=t, pH=b.pH, E=b.E, E_ladder=synth.e_ladder(4), pH_ladder=[b.pH[0]], seed=5,
+                         mc_every=5, ex_every=20)
+    sim.run(60)
+    sim.sync()
+    ctx, st, S, sites = _setup(pkg, b, seed=5, mc_every=5, ex_every=20, with_sites=True)
+    ctx.md_segment(st, sites, 60)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    assert sim.step == 60 and st.step == 60
+    assert torch.equal(sim.xyzq, S["xyzq"]) and torch.equal(sim.vel, S["vel"])
+    assert torch.equal(sim.state, S["state"]) and torch.equal(sim.grid, S["grid"])
+    E = sim.energies().cpu().numpy()
+    assert E.shape == (4, 3) and np.all(np.isfinite(E))
