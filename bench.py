@@ -381,6 +381,10 @@ def main():
     S = Setup(pkg, b, dev, seed=1234 + rank, params=params)
     if not args.no_autotune:
         S.ctx.autotune(S.xyzq, S.rad)
+        # register caps re-tuned on MD segments of this batch (state restored); trial
+        # segments of about 50 ms at ~1.5e11 pair interactions/s
+        est_step_s = 3.0 * max(b.pairs_per_eval(), 1) / 1.5e11
+        S.ctx.autotune_md(S.st, S.sites, trial_steps=int(min(MD_PER_STEP, max(2, 0.05 / est_step_s))))
     persistent = args.persistent
     S.ctx.set_persistent(persistent)
     stream = torch.cuda.current_stream()

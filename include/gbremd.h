@@ -297,6 +297,16 @@ int gb_md_init(gb_ctx* ctx, gb_md_state* state, void* stream);
 int gb_md_segment(gb_ctx* ctx, gb_md_state* state, const gb_sites* sites, int64_t nsteps,
                   void* stream);
 
+/* The register caps tuned on the MD driver itself: coordinate descent over
+ * the three passes' caps, every candidate timed (CUDA events, best of four) on
+ * an MD segment of trial_steps steps (gb_md_segment with these sites, as the
+ * caller will run it), each starting from a copy of the state.  The state
+ * buffers and the state struct are put back as they were before the call
+ * returns; the chosen caps stay on the context (gb_get_reg_caps).  Needs
+ * forces at the incoming coordinates (after gb_md_init).  Allocates a copy
+ * of the state.  GB_ERR_INVALID_ARG for trial_steps outside 1..100000. */
+int gb_autotune_md(gb_ctx* ctx, gb_md_state* state, const gb_sites* sites, int64_t trial_steps, void* stream);
+
 /* Allocation-free energy / force evaluation of ONE molecule.
  *
  * The paper has no counterpart: this is a service for callers that cannot

@@ -119,6 +119,7 @@ def load(path: Optional[str] = None):
         "gb_pass_times": [_P, C.POINTER(C.c_double)],
         "gb_set_persistent": [_P, i32],
         "gb_set_wait_limit": [_P, C.c_int64],
+        "gb_autotune_md": [_P, C.POINTER(MDState), C.POINTER(Sites), C.c_int64, _P],
         "gb_persist_times": [_P, C.POINTER(C.c_double)],
     }
     for name, args in sig.items():
@@ -318,6 +319,12 @@ class Context:
 
     def set_persistent(self, on: bool):
         _check(self.lib.gb_set_persistent(self.h, 1 if on else 0), self.h)
+
+    def autotune_md(self, st: MDState, sites: Optional[SiteTables], trial_steps: int = 100, stream=None):
+        """Register caps tuned on MD segments of trial_steps steps (state restored)."""
+        sp = C.byref(sites.struct) if sites is not None else None
+        _check(self.lib.gb_autotune_md(self.h, C.byref(st), sp, int(trial_steps), _stream(stream)), self.h)
+        return self.reg_caps()
 
     def set_wait_limit(self, polls: int):
         """Polls before a persistent-kernel dependency wait gives up (0: default)."""

@@ -1123,6 +1123,98 @@ extern "C" int gb_set_persistent(gb_ctx* c, int32_t enable) {
     return GB_OK;
 }
 
+// Register caps tuned on the MD driver itself: coordinate descent over the
+// three passes' caps, each candidate timed on short MD segments (CUDA events
+// around the captured graphs, the same launches the driver uses), every trial
+// starting from a saved copy of the MD state, which is put back at the end.
+extern "C" int gb_autotune_md(gb_ctx* c, gb_md_state* st, const gb_sites* sites, int64_t trial_steps,
+                              void* stream) {
+    int rc = check_md(c, st);
+    if (rc) return rc;
+    if (sites && (rc = check_sites(c, sites))) return rc;
+    if (trial_steps < 1 || trial_steps > 100000) return fail(c, GB_ERR_INVALID_ARG, "trial_steps must be 1..100000");
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t N = (size_t)c->N, M = (size_t)c->M;
+    const size_t n_sites = (sites && st->state) ? (size_t)sites->n_sites : 0;
+    struct Buf { void* p; size_t bytes; };
+    const Buf bufs[] = {{(void*)st->xyzq, 16 * N}, {(void*)st->vel, 16 * N}, {(void*)st->force, 16 * N},
+                        {(void*)st->R, 4 * N},     {(void*)st->state, 4 * n_sites},
+                        {(void*)st->pH, st->pH ? 8 * M : 0}, {(void*)st->E, st->E ? 8 * M : 0},
+                        {(void*)st->grid, st->grid ? 4 * M : 0}};
+    size_t total = 0;
+    for (const Buf& b : bufs) total += (b.p ? b.bytes : 0);
+    unsigned char* save = nullptr;
+    GB_CHECK(c, cudaMalloc((void**)&save, std::max<size_t>(total, 16)));
+    const gb_md_state st0 = *st;
+    auto copy_state = [&](bool out) -> cudaError_t {
+        size_t off = 0;
+        for (const Buf& b : bufs) {
+            if (!b.p || !b.bytes) continue;
+            cudaError_t e = out ? cudaMemcpyAsync(save + off, b.p, b.bytes, cudaMemcpyDeviceToDevice, s)
+                                : cudaMemcpyAsync(b.p, save + off, b.bytes, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return e;
+            off += b.bytes;
+        }
+        return cudaSuccess;
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = copy_state(true);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    const std::vector<int> caps = c->list_ctr ? std::vector<int>{1, 3} : std::vector<int>{1, 3, 4};
+    auto trial = [&](const int* cap, float* ms) -> int {
+        for (int k = 0; k < 3; ++k) c->tasks.cap[k] = cap[k];
+        if (c->md_exec) { cudaGraphExecDestroy(c->md_exec); c->md_exec = nullptr; c->md_key.clear(); }
+        float best = 1e30f;
+        for (int rep = 0; rep < 5; ++rep) {           // the first run also captures the graph
+            *st = st0;
+            if (copy_state(false) != cudaSuccess) return fail(c, GB_ERR_CUDA, "state restore failed");
+            if (cudaEventRecord(e0, s) != cudaSuccess) return fail(c, GB_ERR_CUDA, "event record failed");
+            int r = gb_md_segment(c, st, sites, trial_steps, stream);
+            if (r) return r;
+            if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+                return fail(c, GB_ERR_CUDA, "event wait failed");
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0) best = std::min(best, t);
+        }
+        *ms = best;
+        return GB_OK;
+    };
+    int best[3] = {c->tasks.cap[0], c->tasks.cap[1], c->tasks.cap[2]};
+    for (int& b : best)
+        if (std::find(caps.begin(), caps.end(), b) == caps.end()) b = 3;
+    float t_best = 0.0f;
+    if (ce != cudaSuccess) rc = cuda_fail(c, ce, "gb_autotune_md set-up");
+    if (!rc) rc = trial(best, &t_best);
+    for (int pass = 0; pass < 3 && !rc; ++pass) {
+        for (int cap : caps) {
+            if (cap == best[pass]) continue;
+            int cand[3] = {best[0], best[1], best[2]};
+            cand[pass] = cap;
+            float t = 0.0f;
+            rc = trial(cand, &t);
+            if (rc) break;
+            if (t < t_best) {
+                t_best = t;
+                for (int k = 0; k < 3; ++k) best[k] = cand[k];
+            }
+        }
+    }
+    // the chosen caps; the state as it was; no graph captured with other caps
+    for (int k = 0; k < 3; ++k) c->tasks.cap[k] = best[k];
+    if (c->md_exec) { cudaGraphExecDestroy(c->md_exec); c->md_exec = nullptr; c->md_key.clear(); }
+    *st = st0;
+    cudaError_t re = copy_state(false);
+    if (re == cudaSuccess) re = cudaStreamSynchronize(s);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(save);
+    if (!rc && re != cudaSuccess) rc = cuda_fail(c, re, "state restore");
+    return rc;
+}
+
 extern "C" int gb_set_wait_limit(gb_ctx* c, int64_t polls) {
     if (!c) return fail(nullptr, GB_ERR_INVALID_ARG, "NULL context");
     if (polls < 0 || polls > 0xffffffffLL) return fail(c, GB_ERR_INVALID_ARG, "polls must be 0 .. 2^32 - 1");

@@ -212,3 +212,30 @@ def test_simulation_driver_equals_the_state_struct_path(pkg):
     assert torch.equal(sim.state, S["state"]) and torch.equal(sim.grid, S["grid"])
     E = sim.energies().cpu().numpy()
     assert E.shape == (4, 3) and np.all(np.isfinite(E))
+
+
+def test_autotune_md_restores_the_state(pkg):
+    """gb_autotune_md times MD segments from a saved state: the state buffers
+    and counters come back unchanged, the chosen caps stay on the context, and
+    the run that follows equals one on a context given those caps by hand."""
+    import torch
+    b = synth.config_eremd(4, 300)
+    ctx, st, S, sites = _setup(pkg, b, seed=3, mc_every=5, ex_every=20, with_sites=True)
+    keys = ("xyzq", "vel", "force", "R", "state", "E", "grid")
+    before = {k: S[k].clone() for k in keys}
+    caps = ctx.autotune_md(st, sites, trial_steps=20)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    assert st.step == 0 and st.attempt == 0
+    for k in keys:
+        assert torch.equal(S[k], before[k]), k
+    assert len(caps) == 3 and all(c in (1, 3, 4) for c in caps)
+    ctx.md_segment(st, sites, 40)
+    ref, st2, S2, sites2 = _setup(pkg, b, seed=3, mc_every=5, ex_every=20, with_sites=True)
+    for p, c in enumerate(caps):
+        ref.set_reg_cap(c, p)
+    ref.md_segment(st2, sites2, 40)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    ref.sync_status()
+    assert torch.equal(S["xyzq"], S2["xyzq"]) and torch.equal(S["state"], S2["state"])
