@@ -996,8 +996,9 @@ __device__ __forceinline__ void walk_task(const PairArgs& A, const int4 t, long 
     typename P::IState is;
     P::load_i(A, base, n, 64 * K, lane, is);
     const int next = (lane + 1) & 31;
-    // EF_CUT: straddling blocks run the pair code with EF_STRADDLE (the task
-    // list holds in-range blocks only, see k_block_list)
+    // EF_CUT: straddling blocks run the pair code with EF_STRADDLE.  The task
+    // list is the block neighbour list (k_block_list: in-range blocks only),
+    // or, without tile boxes, every block, each counted as straddling.
     constexpr int FS = (FLAGS & EF_CUT) ? (FLAGS | EF_STRADDLE) : FLAGS;
     for (int c = 0; c < cnt; ++c) {
         const bool dx = (J == 2 * K);          // see run_tile: entry / exit rotation of a DX block
