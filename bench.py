@@ -376,7 +376,7 @@ def main():
     import paper_1803_09652_gb300 as pkg
     pkg.load()
 
-    params = pkg.default_params(rep_k=10.0, rep_sigma=2.5, **CUTOFFS.get(args.workload, {}))
+    params = pkg.default_params(rep_k=100.0, rep_sigma=2.5, **CUTOFFS.get(args.workload, {}))
     b = workload(args.workload)
     S = Setup(pkg, b, dev, seed=1234 + rank, params=params)
     if not args.no_autotune:

@@ -36,10 +36,10 @@ class Params(C.Structure):
 def default_params(**kw) -> Params:
     """OBC parameters alpha, beta, gamma = 1.0, 0.8, 4.85, offset 0.09 A,
     eps_in 1, eps_out 78.5, no salt (kappa = 0), no cutoffs (rgbmax = cut = 0);
-    MD driver constants (bond k 300 about 1.5 A, soft repulsion k 10 below
+    MD driver constants (bond k 300 about 1.5 A, soft repulsion k 100 below
     2.5 A, 2 fs, 10 / ps, 12 amu, 300 K)."""
     d = dict(alpha=1.0, beta=0.8, gamma=4.85, offset=0.09, eps_in=1.0, eps_out=78.5,
-             bond_k=300.0, bond_r0=1.5, rep_k=10.0, rep_sigma=2.5, dt=0.002, friction=10.0,
+             bond_k=300.0, bond_r0=1.5, rep_k=100.0, rep_sigma=2.5, dt=0.002, friction=10.0,
              mass=12.0, kT=KB * 300.0, kappa=0.0, rgbmax=0.0, cut=0.0)
     d.update(kw)
     return Params(**d)

@@ -182,8 +182,8 @@ def test_cutoff_md_step_matches_oracle(pkg):
     import torch
     dev = device()
     b = synth.random_batch([400, 120, 33], seed=43, sites=False)
-    params = pkg.default_params(rep_k=10.0, rep_sigma=2.5, rgbmax=9.0, cut=8.0)
-    p = oracle_params(rep_k=10.0, rep_sigma=2.5, rgbmax=9.0, cut=8.0)
+    params = pkg.default_params(rep_k=100.0, rep_sigma=2.5, rgbmax=9.0, cut=8.0)
+    p = oracle_params(rep_k=100.0, rep_sigma=2.5, rgbmax=9.0, cut=8.0)
     ctx = pkg.Context(b.atom_off, params)
     N, M = b.n_atoms, b.n_rep
     S = dict(xyzq=torch.as_tensor(b.xyzq(), device=dev), rad=torch.as_tensor(b.rad_screen(), device=dev),

@@ -22,7 +22,7 @@ def pkg():
 def _setup(pkg, b, seed, mc_every=0, ex_every=0, with_sites=False, persistent=False):
     import torch
     dev = device()
-    params = pkg.default_params(rep_k=10.0, rep_sigma=2.5)
+    params = pkg.default_params(rep_k=100.0, rep_sigma=2.5)
     ctx = pkg.Context(b.atom_off, params)
     ctx.set_persistent(persistent)
     N, M = b.n_atoms, b.n_rep
@@ -61,7 +61,7 @@ def test_one_baoab_step_matches_oracle(pkg, persistent):
     ctx, st, S, _ = _setup(pkg, b, seed=5, persistent=persistent)
     torch.cuda.synchronize()
     x, q, rho, scr, off = oracle.batch_arrays(b)
-    p = oracle_params(rep_k=10.0, rep_sigma=2.5)
+    p = oracle_params(rep_k=100.0, rep_sigma=2.5)
     F0, _ = oracle.forces_all(off, x, q, rho, scr, p)
     assert np.abs(S["force"][:, :3].cpu().numpy() - F0).max() <= F_ABS
     ctx.md_segment(st, None, 1)
@@ -198,7 +198,7 @@ def test_simulation_driver_equals_the_state_struct_path(pkg):
     import torch
     b = synth.config_eremd(4, 300)
     t = b.site_tables(oracle.site_reference_energies(b, oracle_params()))
-    sim = pkg.Simulation(b.atom_off, b.xyzq(), b.rad_screen(), pkg.default_params(rep_k=10.0, rep_sigma=2.5),
+    sim = pkg.Simulation(b.atom_off, b.xyzq(), b.rad_screen(), pkg.default_params(rep_k=100.0, rep_sigma=2.5),
                          sites=t, pH=b.pH, E=b.E, E_ladder=synth.e_ladder(4), pH_ladder=[b.pH[0]], seed=5,
                          mc_every=5, ex_every=20)
     sim.run(60)
@@ -239,3 +239,29 @@ def test_autotune_md_restores_the_state(pkg):
     ctx.sync_status()
     ref.sync_status()
     assert torch.equal(S["xyzq"], S2["xyzq"]) and torch.equal(S["state"], S2["state"])
+
+
+@pytest.mark.parametrize("cutoffs", [{}, dict(rgbmax=12.0, cut=12.0)])
+def test_langevin_driver_holds_the_temperature(pkg, cutoffs):
+    """2000 BAOAB steps of 8 x 2048 atoms from rest with MC and exchanges: the
+    kinetic temperature sum m v^2 / (3 N k_B) over the second half is 300 K
+    within 3 % (the thermostat's target; 3N degrees of freedom, no
+    constraints; BAOAB's full-step velocities read a little low at 2 fs), and
+    nothing diverges."""
+    import torch
+    b = synth.config_eremd(8, 2048)
+    t = b.site_tables(oracle.site_reference_energies(synth.Batch(b.replicas[:1], pH=b.pH[:1], E=b.E[:1]),
+                                                     oracle_params()).tolist() * 8)
+    sim = pkg.Simulation(b.atom_off, b.xyzq(), b.rad_screen(),
+                         pkg.default_params(rep_k=100.0, rep_sigma=2.5, **cutoffs), sites=t, pH=b.pH, E=b.E,
+                         E_ladder=synth.e_ladder(8), pH_ladder=[b.pH[0]], seed=11)
+    sim.run(1000)
+    temps = []
+    for _ in range(10):
+        sim.run(100)
+        v = sim.vel[:, :3].double()
+        ke = 0.5 * 12.0 * (v * v).sum().item() / 418.4          # kcal/mol (amu A^2/ps^2 -> kcal/mol)
+        temps.append(2.0 * ke / (3.0 * b.n_atoms * pkg.KB))
+    sim.sync()
+    assert torch.isfinite(sim.xyzq).all()
+    assert abs(np.mean(temps) / 300.0 - 1.0) < 0.03, temps

@@ -94,7 +94,7 @@ def test_sweep_in_md_driver_keeps_charges_consistent(pkg):
     p = oracle_params()
     G = oracle.site_reference_energies(synth.Batch(b.replicas[:1], pH=b.pH[:1], E=b.E[:1]), p)
     t = b.site_tables(np.tile(G, 4))
-    ctx = pkg.Context(b.atom_off, pkg.default_params(rep_k=10.0, rep_sigma=2.5))
+    ctx = pkg.Context(b.atom_off, pkg.default_params(rep_k=100.0, rep_sigma=2.5))
     sites = pkg.SiteTables(t, 4, dev)
     N = b.n_atoms
     S = dict(xyzq=torch.as_tensor(b.xyzq(), device=dev), rad=torch.as_tensor(b.rad_screen(), device=dev),

@@ -60,7 +60,7 @@ def test_static_entry_matches_context_entry_twice(lib):
     import torch
     import paper_1803_09652_gb300 as pkg
     dev = device()
-    params = pkg.default_params(rep_k=10.0, rep_sigma=2.5)
+    params = pkg.default_params(rep_k=100.0, rep_sigma=2.5)
     mols = [synth.random_batch([700], seed=31), synth.random_batch([1500], seed=32)]
     refs = []
     for b in mols:
