@@ -102,17 +102,20 @@ const char* gb_last_error(const gb_ctx* ctx);
  * Returns GB_OK or the GB_ERR_* code a kernel recorded. */
 int gb_sync_status(gb_ctx* ctx, void* stream);
 
-/* Tile configuration of the pair kernels: warps per block and block pairs
- * (32 x 32 atom tiles) per warp task.  gb_autotune times the candidates on
- * the given inputs and keeps the fastest; gb_set_tiles forces one. */
+/* Tile configuration of the pair kernels: warps per block and blocks (64 x 32
+ * atoms) per warp task of the static task list (a pass with a cutoff walks
+ * its neighbour list instead, in runs of up to 16 blocks).  gb_autotune times
+ * the candidates and register caps pass by pass on the given inputs and
+ * keeps the fastest; gb_set_tiles forces one. */
 int gb_autotune(gb_ctx* ctx, const float* xyzq, const float* rad_screen, void* stream);
 int gb_set_tiles(gb_ctx* ctx, int32_t warps_per_block, int32_t tiles_per_task);
 /* Register cap of the pair kernel of one pass (0 Born radii, 1 energy and
  * direct forces, 2 Born chain rule; -1 = all three), as 256-thread blocks
  * per SM: 1 = the compiler's choice, 3 = at most 80 registers per thread,
  * 4 = at most 64 (more resident warps, more spills; a pass with a cutoff
- * runs cap 3 instead).  gb_autotune picks each pass's cap; the default is 3.
- * GB_ERR_INVALID_ARG for other values. */
+ * runs cap 3 instead).  gb_autotune picks each pass's cap and gb_autotune_md
+ * re-tunes them on MD segments; the default is 3.  GB_ERR_INVALID_ARG for
+ * other values. */
 int gb_set_reg_cap(gb_ctx* ctx, int32_t pass, int32_t min_blocks_per_sm);
 /* The three caps in pass order into caps[3] (host memory). */
 int gb_get_reg_caps(const gb_ctx* ctx, int32_t* caps);
