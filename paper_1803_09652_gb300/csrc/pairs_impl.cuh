@@ -354,7 +354,7 @@ __device__ __forceinline__ void load_xas(const PairArgs& A, int64_t base, int n,
 // --- pass 1: Born integrals I_i = sum_j H(r_ij; a_i, s_j) -----------------------
 struct Born {
     static constexpr int NQ = 1;      // int64 i-side accumulators per atom (shared memory)
-    static constexpr int UNROLL = 1;  // rotation steps unrolled (measured best per pass)
+    static constexpr int UNROLL = 2;  // rotation steps unrolled (measured best per pass)
     static constexpr bool RADIUS_CUT = true;   // EF_CUT: the cutoff is rgbmax
     struct IState {
         f2 nx, ny, nz, a, s, s2, hs3;   // nx = -x
@@ -485,7 +485,7 @@ struct Born {
 // exp(-D) = 2^(r^2 (-h_i) h_j) is two multiplies and one ex2.
 struct Energy {
     static constexpr int NQ = 5;      // fx, fy, fz, dE/dR, dE/dq (shared memory)
-    static constexpr int UNROLL = 1;
+    static constexpr int UNROLL = 2;
     static constexpr bool RADIUS_CUT = false;  // EF_CUT: the cutoff is `cut`
     struct IState {
         f2 nx, ny, nz, q, R, nh;
