@@ -1,0 +1,42 @@
+"""Host logic of bench.py that shapes its JSON line: the pair count of a
+workload with a pair cutoff (k-d tree count against brute force), the
+launches counted per MD segment, and the workload table."""
+import numpy as np
+import pytest
+
+import bench
+import synth
+
+
+def test_pairs_within_matches_brute_force():
+    b = synth.random_batch([300, 0, 77, 1], seed=61, sites=False)
+    for cut in (3.0, 8.0, 1e4):
+        brute = 0
+        for rep in b.replicas:
+            x = rep.xyz.astype(np.float64)
+            d = np.linalg.norm(x[:, None] - x[None], axis=2)
+            brute += int(np.sum(d[np.triu_indices(len(x), 1)] < cut))
+        assert synth.pairs_within(b, cut) == brute
+    assert synth.pairs_within(b, 1e4) == b.pairs_per_eval()
+
+
+def test_pairs_per_md_step_counts_within_the_cutoff_only_with_a_cutoff():
+    b = synth.random_batch([200, 90], seed=62, sites=False)
+    assert bench.pairs_per_md_step(b, "eremd_8x2048") == b.pairs_per_eval()
+    cut = bench.CUTOFFS["cutoff_1x100000"]["cut"]
+    assert bench.pairs_per_md_step(b, "cutoff_1x100000") == synth.pairs_within(b, cut)
+
+
+@pytest.mark.parametrize("cutoff,per_step", [(False, 6), (True, 8)])
+def test_launches_per_segment(cutoff, per_step):
+    n = 100
+    mc = 4 * (n // bench.MC_EVERY)
+    ex = 2 * (n // bench.EX_EVERY)
+    assert bench.launches_per_segment(n, False, cutoff) == 1 + per_step * n + 1 + mc + ex + 1
+    assert bench.launches_per_segment(n, True) == 1 + n // bench.MC_EVERY + mc + ex + 1
+
+
+def test_every_workload_is_known():
+    assert set(bench.CUTOFFS) <= set(bench.WORKLOADS)
+    with pytest.raises(ValueError):
+        bench.workload("no_such_workload")
