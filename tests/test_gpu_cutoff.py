@@ -244,6 +244,7 @@ def test_cutoff_static_entry_matches_oracle(pkg):
 
 
 def test_invalid_cutoffs_are_rejected(pkg):
+    device()                                   # skips without a GPU
     b = synth.random_batch([64], seed=45)
     for kw in (dict(rgbmax=-1.0), dict(cut=-2.0), dict(cut=float("nan")), dict(rgbmax=float("inf"))):
         with pytest.raises(RuntimeError):
@@ -289,3 +290,26 @@ def test_cutoff_skips_out_of_range_blocks_on_a_large_chain(pkg):
     assert np.abs(F.sum(0)).max() <= 1e-6 * np.abs(F).sum() + 1e-3
     qp = b.xyzq()[:, 3].astype(np.float64) * o["dEdq"]
     assert abs(qp.sum() - 2 * (o["E"][0, 0] + o["E"][0, 1])) <= 2e-6 * np.abs(qp).sum()
+
+
+def test_autotune_md_with_cutoffs_keeps_the_state_and_valid_caps(pkg):
+    """On a context with cutoffs the MD-level autotuner tries only the caps the
+    cutoff kernels have (1, 3) and puts the MD state back."""
+    device()                                   # skips without a GPU
+    import torch
+    b = synth.config_eremd(2, 600)
+    t = b.site_tables(oracle.site_reference_energies(b, oracle_params()))
+    sim = pkg.Simulation(b.atom_off, b.xyzq(), b.rad_screen(),
+                         pkg.default_params(rep_k=100.0, rep_sigma=2.5, rgbmax=9.0, cut=9.0), sites=t,
+                         pH=b.pH, E=b.E, E_ladder=synth.e_ladder(2), pH_ladder=[b.pH[0]], seed=4,
+                         mc_every=5, ex_every=10)
+    before = {k: getattr(sim, k).clone() for k in ("xyzq", "vel", "force", "state", "E", "grid")}
+    caps = sim.ctx.autotune_md(sim.st, sim.sites, trial_steps=10)
+    sim.sync()
+    assert all(c in (1, 3) for c in caps)
+    assert sim.step == 0
+    for k, v in before.items():
+        assert torch.equal(getattr(sim, k), v), k
+    sim.run(20)
+    sim.sync()
+    assert torch.isfinite(sim.xyzq).all()

@@ -146,6 +146,7 @@ def test_persistent_wait_that_runs_out_reports_a_timeout(pkg):
     gb_sync_status reports GB_ERR_TIMEOUT, and after the default limit is
     restored the same context runs the same segment to the same result as the
     multi-launch path."""
+    device()                                   # skips without a GPU
     import torch
     b = synth.random_batch([2048, 1500], seed=21, sites=False)
     ctx, st, S, _ = _setup(pkg, b, seed=8, persistent=True)
@@ -195,6 +196,7 @@ def test_simulation_driver_equals_the_state_struct_path(pkg):
     """pkg.Simulation (the Python driver) runs the same MD, MC and exchanges as
     a gb_md_state filled by hand: identical coordinates, site states and
     exchange grid after 60 steps."""
+    device()                                   # skips without a GPU
     import torch
     b = synth.config_eremd(4, 300)
     t = b.site_tables(oracle.site_reference_energies(b, oracle_params()))
@@ -218,6 +220,7 @@ def test_autotune_md_restores_the_state(pkg):
     """gb_autotune_md times MD segments from a saved state: the state buffers
     and counters come back unchanged, the chosen caps stay on the context, and
     the run that follows equals one on a context given those caps by hand."""
+    device()                                   # skips without a GPU
     import torch
     b = synth.config_eremd(4, 300)
     ctx, st, S, sites = _setup(pkg, b, seed=3, mc_every=5, ex_every=20, with_sites=True)
@@ -248,6 +251,7 @@ def test_langevin_driver_holds_the_temperature(pkg, cutoffs):
     within 3 % (the thermostat's target; 3N degrees of freedom, no
     constraints; BAOAB's full-step velocities read a little low at 2 fs), and
     nothing diverges."""
+    device()                                   # skips without a GPU
     import torch
     b = synth.config_eremd(8, 2048)
     t = b.site_tables(oracle.site_reference_energies(synth.Batch(b.replicas[:1], pH=b.pH[:1], E=b.E[:1]),
@@ -265,3 +269,25 @@ def test_langevin_driver_holds_the_temperature(pkg, cutoffs):
     sim.sync()
     assert torch.isfinite(sim.xyzq).all()
     assert abs(np.mean(temps) / 300.0 - 1.0) < 0.03, temps
+
+
+def test_simulation_in_sweep_mode_keeps_charges_consistent(pkg):
+    """Simulation with mc_mode 1 (every residue once per halt): after a run the
+    charges of every site are those of its state."""
+    device()                                   # skips without a GPU
+    b = synth.config_eremd(4, 300)
+    t = b.site_tables(oracle.site_reference_energies(b, oracle_params()))
+    sim = pkg.Simulation(b.atom_off, b.xyzq(), b.rad_screen(), pkg.default_params(rep_k=100.0, rep_sigma=2.5),
+                         sites=t, pH=b.pH, E=b.E, E_ladder=synth.e_ladder(4), pH_ladder=[b.pH[0]], seed=6,
+                         mc_every=5, ex_every=20, mc_mode=1)
+    sim.run(100)
+    sim.sync()
+    x = sim.xyzq.cpu().numpy()
+    st = sim.state.cpu().numpy()
+    assert st.any()
+    for s in range(t["n_sites"]):
+        r = np.searchsorted(t["site_off"], s, side="right") - 1
+        a0, a1 = t["site_atom_off"][s], t["site_atom_off"][s + 1]
+        idx = t["site_atom_idx"][a0:a1] + b.atom_off[r]
+        qo = t["site_q_off"][s] + st[s] * (a1 - a0)
+        assert np.array_equal(x[idx, 3], t["q_state"][qo:qo + a1 - a0])
