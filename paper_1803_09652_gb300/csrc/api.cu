@@ -823,7 +823,8 @@ int enqueue_exchange(gb_ctx* c, gb_md_state* st, const gb_sites* sites, cudaStre
 // Enqueue `len` MD steps (with their MC attempts and exchanges) on stream s.
 // Steps are numbered from the device counter ctr[0]; the last node advances it.
 // With the persistent kernel every run of steps up to the next MC / exchange
-// point is one launch; otherwise each step is seven launches.
+// point is one launch; otherwise each step is six launches (eight with a
+// cutoff: the neighbour list's reset and build).
 int enqueue_steps(gb_ctx* c, gb_md_state* st, const gb_sites* sites, int64_t len, cudaStream_t s) {
     const float* xyzq = st->xyzq;
     const float* rad = st->rad_screen;
