@@ -17,8 +17,12 @@
  *    valid once the stream reaches that point.
  *  - Return value: GB_OK (0) or a negative GB_ERR_* code.  Argument and launch
  *    errors are reported synchronously; gb_last_error() has the message.
- *    Errors detected on the device (a bounded wait that gave up, non-finite
- *    input) set a device error word that gb_sync_status() reads and clears.
+ *    Errors detected on the device set a device error word that
+ *    gb_sync_status() reads and clears (the first one recorded is kept):
+ *    GB_ERR_NONFINITE for a non-finite coordinate, charge or Born radius, or
+ *    two atoms of a replica closer than 1e-4 A (coincident); GB_ERR_TIMEOUT
+ *    for a bounded wait that gave up; GB_ERR_INVALID_ARG for a site table
+ *    that fails the checks listed at gb_sites.
  *  - Per-atom layouts:
  *      xyzq        float[N][4]   x, y, z, charge q
  *      rad_screen  float[N][2]   intrinsic radius rho, HCT screening factor S
@@ -163,7 +167,13 @@ int gb_energy_forces(gb_ctx* ctx, const float* xyzq, const float* rad_screen, fl
  *   G_ref (double)      Delta G_elec,ref term of Eq. 8 / 9 as a per-state value;
  *                       the change of state k -> k' subtracts G_ref[k'] - G_ref[k]
  *   n_H, n_e            protons / electrons bound in each state
- *   pKa_ref, E0_ref     per site (double; E0_ref in V) */
+ *   pKa_ref, E0_ref     per site (double; E0_ref in V)
+ * The tables stay on the device and are not read on the host.  The kernels
+ * check, before any access through them, that the atom indices of every site
+ * they touch lie in [0, n) of its replica, that nstates >= 2 and that the
+ * current state lies in [0, nstates).  An attempt or exchange that fails a
+ * check is skipped, leaves charges and states unchanged and records
+ * GB_ERR_INVALID_ARG for gb_sync_status. */
 typedef struct {
     int32_t n_rep;
     int32_t n_sites;
@@ -254,7 +264,9 @@ int eremd_exchange(int32_t n_ladders, int32_t ladder_len, int32_t ladder_stride,
                    uint8_t* acc_out, void* stream);
 
 /* Electrons (kind 1) or protons (kind 0) bound by each replica's sites in
- * the given states: n_count_out int32[M]. */
+ * the given states: n_count_out int32[M].  A replica with a site of that
+ * kind whose state lies outside [0, site_nstates) gets -1, and no table entry
+ * past the site's states is read. */
 int gb_count_bound(const gb_sites* sites, const int32_t* state, int32_t kind,
                    int32_t* n_count_out, void* stream);
 

@@ -702,7 +702,9 @@ extern "C" int eremd_exchange(int32_t n_ladders, int32_t len, int32_t ladder_str
 extern "C" int gb_count_bound(const gb_sites* s, const int32_t* state, int32_t kind,
                               int32_t* out, void* stream) {
     if (!s || !state || !out || !s->site_off) return fail(nullptr, GB_ERR_INVALID_ARG, "NULL argument");
-    cudaError_t e = gbk::launch_count(s->site_off, s->site_kind, s->site_state_off, s->n_H, s->n_e,
+    if (s->n_sites > 0 && (!s->site_kind || !s->site_nstates || !s->site_state_off || !s->n_H || !s->n_e))
+        return fail(nullptr, GB_ERR_INVALID_ARG, "a site table pointer is NULL");
+    cudaError_t e = gbk::launch_count(s->site_off, s->site_kind, s->site_nstates, s->site_state_off, s->n_H, s->n_e,
                                       state, kind, s->n_rep, out, (cudaStream_t)stream);
     if (e != cudaSuccess) return fail(nullptr, GB_ERR_CUDA, cudaGetErrorString(e));
     return GB_OK;
@@ -804,11 +806,13 @@ int enqueue_exchange(gb_ctx* c, gb_md_state* st, const gb_sites* sites, cudaStre
     x.grid = st->grid;
     x.site_off = sites->site_off;
     x.site_kind = sites->site_kind;
+    x.site_nstates = sites->site_nstates;
     x.site_state_off = sites->site_state_off;
     x.n_H = sites->n_H;
     x.n_e = sites->n_e;
     x.state = st->state;
     x.ctr = c->ctr;
+    x.err = c->err;
     x.ex_dim = st->ex_dim;
     x.wrap = st->wrap;
     x.seed = st->seed;

@@ -206,6 +206,25 @@ __device__ __forceinline__ MCPick mc_pick(const MCArgs& A, int r) {
     return pk;
 }
 
+// Site table checks of an attempt, by the whole block before any access
+// through the table: every atom index of the site inside the replica
+// (0 <= idx < n), at least two states, the current state among them.  On a
+// violation the attempt is skipped and GB_ERR_INVALID_ARG recorded.
+__device__ bool mc_site_ok(const MCArgs& A, const MCPick& pk, int a0, int na, int n) {
+    bool bad = false;
+    for (int k = threadIdx.x; k < na; k += blockDim.x) {
+        const int idx = A.site_atom_idx[a0 + k];
+        bad |= idx < 0 || idx >= n;
+    }
+    if (threadIdx.x == 0) {
+        const int ns = A.site_nstates[pk.site];
+        bad |= ns < 2 || pk.cur < 0 || pk.cur >= ns;
+    }
+    bad = __syncthreads_or(bad);
+    if (bad && threadIdx.x == 0 && A.err) atomicCAS(A.err, 0, GB_ERR_INVALID_ARG);
+    return !bad;
+}
+
 // (R, 1/(2R)) of atom g, from whichever radius buffer the caller gave.
 __device__ __forceinline__ float2 mc_Rh(const MCArgs& A, int64_t g) {
     if (A.R) {
@@ -248,6 +267,7 @@ __global__ void __launch_bounds__(256) k_mc_rows(MCArgs A) {
     if (na > MC_MAX_SITE_ATOMS || na < 1) return;
     const int64_t base = A.atom_off[r];
     const int n = (int)(A.atom_off[r + 1] - base);
+    if (!mc_site_ok(A, s_pick, a0, na, n)) return;
     const int j0 = part * MC_CHUNK, j1 = min(n, j0 + MC_CHUNK);
     const float tke = (float)A.tau_ke, kc = (float)A.kc, keo = (float)A.ke_out, kap = (float)A.kappa;
     double* out = A.phi_part + ((size_t)r * A.n_parts + part) * MC_MAX_SITE_ATOMS;
@@ -283,15 +303,18 @@ __global__ void __launch_bounds__(256) k_mc_decide(MCArgs A) {
     const int site = s_pick.site;
     const int a0 = site >= 0 ? A.site_atom_off[site] : 0;
     const int na = site >= 0 ? A.site_atom_off[site + 1] - a0 : 0;
-    if (site < 0 || na > MC_MAX_SITE_ATOMS || na < 1) {
+    const int64_t base = A.atom_off[r];
+    const int n = (int)(A.atom_off[r + 1] - base);
+    bool usable = site >= 0 && na <= MC_MAX_SITE_ATOMS && na >= 1;
+    if (usable) usable = mc_site_ok(A, s_pick, a0, na, n);
+    if (!usable) {
         if (tid == 0) {
             if (A.dG_out) A.dG_out[r] = site < 0 ? 0.0 : __longlong_as_double(0x7ff8000000000000LL);
             if (A.acc_out) A.acc_out[r] = 0;
+            if (site >= 0 && (na > MC_MAX_SITE_ATOMS || na < 1) && A.err) atomicCAS(A.err, 0, GB_ERR_INVALID_ARG);
         }
         return;
     }
-    const int64_t base = A.atom_off[r];
-    const int n = (int)(A.atom_off[r + 1] - base);
     const int n_parts_r = (n + MC_CHUNK - 1) / MC_CHUNK;
     const int qo = A.site_q_off[site] + s_pick.nxt * na;
     for (int k = tid; k < na; k += blockDim.x) {
@@ -385,12 +408,26 @@ __device__ bool sweep_list(const MCArgs& A, int r, SweepList& L) {
     }
     __syncthreads();
     if (!s_ok) return false;
+    // the table checks of mc_site_ok for every listed site
+    const int n = (int)(A.atom_off[r + 1] - A.atom_off[r]);
+    bool bad = false;
     for (int k = 0; k < L.n_sites; ++k) {
         const int a0 = A.site_atom_off[L.site[k]];
-        for (int a = threadIdx.x; a < L.first[k + 1] - L.first[k]; a += blockDim.x)
-            L.atom[L.first[k] + a] = A.site_atom_idx[a0 + a];
+        for (int a = threadIdx.x; a < L.first[k + 1] - L.first[k]; a += blockDim.x) {
+            const int idx = A.site_atom_idx[a0 + a];
+            bad |= idx < 0 || idx >= n;
+            L.atom[L.first[k] + a] = idx;
+        }
     }
-    __syncthreads();
+    for (int k = threadIdx.x; k < L.n_sites; k += blockDim.x) {
+        const int ns = A.site_nstates[L.site[k]], cur = A.state[L.site[k]];
+        bad |= ns < 2 || cur < 0 || cur >= ns;
+    }
+    bad = __syncthreads_or(bad);
+    if (bad) {
+        if (threadIdx.x == 0 && A.err) atomicCAS(A.err, 0, GB_ERR_INVALID_ARG);
+        return false;
+    }
     return true;
 }
 
@@ -581,12 +618,19 @@ __global__ void k_exchange(ExArgs A) {
                   a, b, attempt, A.seed, A.value_of_rep, A.delta_out, A.acc_out);
 }
 
-__device__ __forceinline__ int bound_count(const GridExArgs& A, int rep, int kind) {
+// Bound electrons (kind 1) or protons (kind 0) of replica rep; -1 when a
+// site of that kind has a state outside [0, nstates).
+__device__ __forceinline__ int bound_count(const int32_t* site_off, const int32_t* site_kind,
+                                           const int32_t* site_nstates, const int32_t* site_state_off,
+                                           const int32_t* n_H, const int32_t* n_e, const int32_t* state,
+                                           int rep, int kind) {
     int c = 0;
-    for (int s = A.site_off[rep]; s < A.site_off[rep + 1]; ++s) {
-        if (A.site_kind[s] != kind) continue;
-        const int so = A.site_state_off[s] + A.state[s];
-        c += kind ? A.n_e[so] : A.n_H[so];
+    for (int s = site_off[rep]; s < site_off[rep + 1]; ++s) {
+        if (site_kind[s] != kind) continue;
+        const int st = state[s];
+        if (st < 0 || st >= site_nstates[s]) return -1;
+        const int so = site_state_off[s] + st;
+        c += kind ? n_e[so] : n_H[so];
     }
     return c;
 }
@@ -610,7 +654,13 @@ __global__ void k_grid_exchange(GridExArgs A) {
     const int kind = dimE ? 1 : 0;
     const double* values = dimE ? A.E_ladder : A.pH_ladder;
     const double c = dimE ? FARADAY / A.kT : LN10;
-    const double delta = c * (values[b] - values[a]) * (double)(bound_count(A, i, kind) - bound_count(A, j, kind));
+    const int ci = bound_count(A.site_off, A.site_kind, A.site_nstates, A.site_state_off, A.n_H, A.n_e, A.state, i, kind);
+    const int cj = bound_count(A.site_off, A.site_kind, A.site_nstates, A.site_state_off, A.n_H, A.n_e, A.state, j, kind);
+    if (ci < 0 || cj < 0) {                 // corrupt state: no exchange for this pair
+        if (A.err) atomicCAS(A.err, 0, GB_ERR_INVALID_ARG);
+        return;
+    }
+    const double delta = c * (values[b] - values[a]) * (double)(ci - cj);
     const Philox4 w = philox4x64((u64)(l * len + a), attempt, 3, 0, A.seed, 0);
     const int acc = (delta <= 0.0) || (unif53(w.w[0]) < exp(-delta));
     if (acc) { *pa = j; *pb = i; }
@@ -619,19 +669,13 @@ __global__ void k_grid_exchange(GridExArgs A) {
     vr[*pb] = values[b];
 }
 
-__global__ void k_count(const int32_t* site_off, const int32_t* site_kind, const int32_t* site_state_off,
-                        const int32_t* n_H, const int32_t* n_e, const int32_t* state, int32_t kind,
-                        int32_t M, int32_t* out) {
+__global__ void k_count(const int32_t* site_off, const int32_t* site_kind, const int32_t* site_nstates,
+                        const int32_t* site_state_off, const int32_t* n_H, const int32_t* n_e,
+                        const int32_t* state, int32_t kind, int32_t M, int32_t* out) {
     pdl_enter();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= M) return;
-    int c = 0;
-    for (int s = site_off[r]; s < site_off[r + 1]; ++s) {
-        if (site_kind[s] != kind) continue;
-        const int so = site_state_off[s] + state[s];
-        c += kind ? n_e[so] : n_H[so];
-    }
-    out[r] = c;
+    out[r] = bound_count(site_off, site_kind, site_nstates, site_state_off, n_H, n_e, state, r, kind);
 }
 
 // --- launchers -----------------------------------------------------------------------
@@ -687,13 +731,13 @@ cudaError_t launch_grid_exchange(const GridExArgs& a, cudaStream_t s) {
     return launch_pdl(k_grid_exchange, dim3((n + 255) / 256), dim3(256), 0, s, a);
 }
 
-cudaError_t launch_count(const int32_t* site_off, const int32_t* site_kind,
+cudaError_t launch_count(const int32_t* site_off, const int32_t* site_kind, const int32_t* site_nstates,
                          const int32_t* site_state_off, const int32_t* n_H, const int32_t* n_e,
                          const int32_t* state, int32_t kind, int32_t M, int32_t* out,
                          cudaStream_t s) {
     if (M == 0) return cudaSuccess;
-    return launch_pdl(k_count, dim3((M + 127) / 128), dim3(128), 0, s, site_off, site_kind, site_state_off, n_H,
-                      n_e, state, kind, M, out);
+    return launch_pdl(k_count, dim3((M + 127) / 128), dim3(128), 0, s, site_off, site_kind, site_nstates,
+                      site_state_off, n_H, n_e, state, kind, M, out);
 }
 
 }  // namespace gbk

@@ -220,11 +220,13 @@ struct GridExArgs {
     int32_t* grid;
     const int32_t* site_off;
     const int32_t* site_kind;
+    const int32_t* site_nstates;
     const int32_t* site_state_off;
     const int32_t* n_H;
     const int32_t* n_e;
     const int32_t* state;
     const u64* ctr;
+    int* err;                  // GB_ERR_INVALID_ARG on a state outside its site's range
     int32_t ex_dim;            // 0 E only, 1 pH only, 2 alternate
     int32_t wrap;
     u64 seed;
@@ -259,7 +261,7 @@ size_t persist_smem();
 cudaError_t persist_occupancy(int rep, int* blocks_per_sm);
 cudaError_t launch_persist(const PersistArgs& a, int rep, int grid, cudaStream_t s);
 
-cudaError_t launch_count(const int32_t* site_off, const int32_t* site_kind,
+cudaError_t launch_count(const int32_t* site_off, const int32_t* site_kind, const int32_t* site_nstates,
                          const int32_t* site_state_off, const int32_t* n_H,
                          const int32_t* n_e, const int32_t* state, int32_t kind, int32_t M,
                          int32_t* out, cudaStream_t s);
