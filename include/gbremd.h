@@ -20,7 +20,7 @@
  *    Errors detected on the device set a device error word that
  *    gb_sync_status() reads and clears (the first one recorded is kept):
  *    GB_ERR_NONFINITE for a non-finite coordinate, charge or Born radius, or
- *    two atoms of a replica closer than 1e-4 A (coincident); GB_ERR_TIMEOUT
+ *    two atoms of a replica at the same position (coincident); GB_ERR_TIMEOUT
  *    for a bounded wait that gave up; GB_ERR_INVALID_ARG for a site table
  *    that fails the checks listed at gb_sites.
  *  - Per-atom layouts:

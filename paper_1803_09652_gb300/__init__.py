@@ -416,6 +416,59 @@ class Simulation:
         """[M, 3] float64 (GB, Coulomb, soft repulsion) at the current coordinates."""
         return self.ctx.energy_forces(self.xyzq, self.rad, want=("E",))["E"]
 
+    # -- checkpoint / resume ------------------------------------------------------------
+    CHECKPOINT_ARRAYS = ("xyzq", "vel", "state", "grid", "pH", "E")
+
+    def checkpoint(self, stream=None) -> dict:
+        """Host copy of the dynamic state: coordinates and charges, velocities,
+        site states, the exchange grid, per-replica pH and E, and the step,
+        attempt and seed counters.  Every random number of the driver is
+        drawn from Philox with counters (replica, step or attempt, purpose),
+        and gb_md_init recomputes the forces at the saved coordinates with the
+        same kernels a step ends with, so restore() followed by run(n) gives
+        bit for bit what this simulation would have given by running on."""
+        import torch
+        if stream is not None:
+            stream.synchronize()
+        torch.cuda.synchronize(self.xyzq.device)
+        ck = {k: getattr(self, k).cpu().numpy().copy() for k in self.CHECKPOINT_ARRAYS}
+        ck["step"] = int(self.st.step)
+        ck["attempt"] = int(self.st.attempt)
+        ck["seed"] = int(self.st.seed)
+        return ck
+
+    def restore(self, ck: dict, stream=None) -> "Simulation":
+        """Loads a checkpoint() of a simulation built with the same arguments
+        (batch layout, parameters, sites, ladders) and re-initialises the
+        forces (gb_md_init)."""
+        import torch
+        for k in self.CHECKPOINT_ARRAYS:
+            dst = getattr(self, k)
+            src = np.asarray(ck[k])
+            if tuple(src.shape) != tuple(dst.shape):
+                raise ValueError(f"checkpoint {k} has shape {src.shape}, the simulation {tuple(dst.shape)}")
+            dst.copy_(torch.as_tensor(src, dtype=dst.dtype))
+        self.st.step = int(ck["step"])
+        self.st.attempt = int(ck["attempt"])
+        self.st.seed = int(ck["seed"])
+        self.ctx.md_init(self.st, stream)
+        return self
+
+
+def save_checkpoint(path: str, ck: dict) -> None:
+    """Writes a Simulation.checkpoint() to an .npz file (no pickled objects)."""
+    arrays = {k: np.asarray(v) for k, v in ck.items()}
+    np.savez(path, **arrays)
+
+
+def load_checkpoint(path: str) -> dict:
+    """Reads a file written by save_checkpoint."""
+    with np.load(path, allow_pickle=False) as f:
+        ck = {k: f[k].copy() for k in f.files}
+    for k in ("step", "attempt", "seed"):
+        ck[k] = int(ck[k])
+    return ck
+
 
 def eremd_exchange(values, rep_at_slot, n_count, dim, attempt, seed, kT, wrap=True,
                    n_ladders=1, ladder_len=None, ladder_stride=None, slot_stride=1,

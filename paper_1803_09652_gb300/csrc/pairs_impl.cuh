@@ -312,11 +312,6 @@ struct BlockInfo {
     float t_near;
     float skip2;      // EF_STRADDLE blocks: a step whose pairs all have r^2 > skip2 adds nothing
 };
-// Two atoms of one replica closer than 1e-4 A count as coincident: the
-// Born pass records GB_ERR_NONFINITE (1/r and the HCT terms lose meaning).
-// Masked pairs (self pairs, pairs past a replica's end) read as far first.
-constexpr float COINCIDENT_R2 = 1e-8f;
-
 struct Mask {
     bool x, y;
 };
@@ -402,7 +397,6 @@ struct Born {
             const bool sh = (!out_ij0 && r.x + j.s > rc) || (!out_ij1 && r.y + j.s > rc) ||
                             (!out_ji0 && r.x + i.s.x > rc) || (!out_ji1 && r.y + i.s.y > rc);
             if (__any_sync(0xffffffffu, sh)) {
-                if (fminf(r2.x, r2.y) < COINCIDENT_R2 && A.err) atomicCAS(A.err, 0, GB_ERR_NONFINITE);
                 const f2 h_ij = keep<MODE>(hct_cut_dir2(r, rinv, i.a, F2(j.s), rc), m);
                 const f2 h_ji = keep<MODE>(hct_cut_dir2(r, rinv, F2(j.a), i.s, rc), m);
                 p.I = add2(p.I, h_ij);
@@ -431,7 +425,6 @@ struct Born {
         f2 h_ij = mul2(F2(0.5f * sj2 * j.s), mul2(rinv4, g_ij));
         f2 h_ji = mul2(i.hs3, mul2(rinv4, g_ji));
         if (__any_sync(0xffffffffu, r2min < bi.t_near)) {
-            if (r2min < COINCIDENT_R2 && A.err) atomicCAS(A.err, 0, GB_ERR_NONFINITE);
             const f2 r = mul2(r2, rinv);
             const f2 lim_ij = add2(i.a, F2(j.s)), lim_ji = add2(F2(j.a), i.s);
             const bool b0 = !far_ok(r.x, lim_ij.x, y_ij.x), b1 = !far_ok(r.y, lim_ij.y, y_ij.y);
@@ -471,7 +464,13 @@ struct Born {
         sa[lane] += fix_i(p.I.x);
         sa[32 + lane] += fix_i(p.I.y);
     }
+    // Two atoms at the same position (r = 0; masked pairs read as far first):
+    // r = r^2 / r is NaN, the closed form carries it through U = r + s and
+    // the restricted form of the cutoff through w = r - s^2/r, so both atoms'
+    // sums turn NaN.  One test per block and lane, on the j side, records it
+    // before the fixed-point conversion would hide it.
     static __device__ __forceinline__ void flush_j(const PairArgs& A, int64_t base, int n, int j, const JState& st) {
+        if (!isfinite(st.acc) && A.err) atomicCAS(A.err, 0, GB_ERR_NONFINITE);
         if (j < n) red_add(&A.I_acc[base + j], fix_i(st.acc));
     }
     static __device__ __forceinline__ void flush_i(const PairArgs& A, int, int64_t base, int n, int i0, int lane,
