@@ -300,6 +300,13 @@ typedef struct {
     int32_t mc_every, ex_every, ex_dim, wrap;
     int32_t mc_mode;        /* 0: one residue per attempt (redox_ph_mc_step, the implicit-
                                solvent scheme); 1: every residue once (redox_ph_mc_sweep) */
+    int64_t* ex_count;      /* nullable, int64[2][2][n_pH * n_E], accumulated by every
+                               exchange: [d][0][g] attempts and [d][1][g] acceptances of the
+                               neighbour pair whose first slot is grid index g (the pair
+                               (g, g+1) along E for d = 0, (g, g+n_E) along pH for d = 1;
+                               the wrap pair has its first slot at the ladder's end).  An
+                               exchange skipped for a corrupt state counts as neither.
+                               The caller zeroes it; gb_autotune_md leaves it as it was. */
 } gb_md_state;
 
 /* Advance the batch by nsteps MD steps.  Step t (1-based, absolute) is

@@ -75,7 +75,7 @@ class MDState(C.Structure):
                 ("kT", C.c_double), ("bond_k", C.c_float), ("bond_r0", C.c_float),
                 ("seed", C.c_uint64), ("step", C.c_uint64), ("attempt", C.c_uint64),
                 ("mc_every", C.c_int32), ("ex_every", C.c_int32), ("ex_dim", C.c_int32),
-                ("wrap", C.c_int32), ("mc_mode", C.c_int32)]
+                ("wrap", C.c_int32), ("mc_mode", C.c_int32), ("ex_count", _P)]
 
 
 _lib = None
@@ -354,8 +354,8 @@ class Simulation:
     pH_ladder: the exchange grid's ladders, replica p * n_E + e starting at pH
     row p and E column e; exchanges run when n_E * n_pH == M > 1, along E
     (ex_dim 0), pH (1) or alternating (2, the default on a 2-D grid).
-    Attributes xyzq, vel, force, R, state, pH, E, grid are the live device
-    tensors."""
+    Attributes xyzq, vel, force, R, state, pH, E, grid and ex_count (the
+    exchange counters of gb_md_state) are the live device tensors."""
 
     def __init__(self, atom_off, xyzq, rad_screen, params: Optional[Params] = None, sites=None, pH=None,
                  E=None, E_ladder=None, pH_ladder=None, *, dt=0.002, friction=10.0, mass=12.0,
@@ -379,6 +379,7 @@ class Simulation:
         self.E_ladder = torch.as_tensor(E_lad, **f64)
         self.pH_ladder = torch.as_tensor(pH_lad, **f64)
         self.grid = torch.arange(M, dtype=torch.int32, device=dev)
+        self.ex_count = torch.zeros((2, 2, M), dtype=torch.int64, device=dev)
         self.sites = SiteTables(sites, M, dev) if sites is not None else None
         n_sites = int(sites["n_sites"]) if sites is not None else 0
         self.state = torch.zeros(max(n_sites, 1), dtype=torch.int32, device=dev)
@@ -397,6 +398,7 @@ class Simulation:
         st.ex_every = ex_every if (ladder and self.sites is not None) else 0
         st.ex_dim = (2 if n_pH > 1 else 0) if ex_dim is None else ex_dim
         st.wrap, st.mc_mode = 1 if wrap else 0, mc_mode
+        st.ex_count = self.ex_count.data_ptr()
         self.st = st
         self.ctx.md_init(st)
 
@@ -417,7 +419,7 @@ class Simulation:
         return self.ctx.energy_forces(self.xyzq, self.rad, want=("E",))["E"]
 
     # -- checkpoint / resume ------------------------------------------------------------
-    CHECKPOINT_ARRAYS = ("xyzq", "vel", "state", "grid", "pH", "E")
+    CHECKPOINT_ARRAYS = ("xyzq", "vel", "state", "grid", "pH", "E", "ex_count")
 
     def checkpoint(self, stream=None) -> dict:
         """Host copy of the dynamic state: coordinates and charges, velocities,
@@ -453,6 +455,54 @@ class Simulation:
         self.st.seed = int(ck["seed"])
         self.ctx.md_init(self.st, stream)
         return self
+
+
+    # -- metrics -------------------------------------------------------------------------
+    def exchange_stats(self) -> dict:
+        """Attempts, acceptances and acceptance ratio of every neighbour pair
+        of the exchange grid so far.  Keys "E" and "pH": arrays
+        [n_pH, n_E] indexed by the pair's first slot (pH row, E column); the
+        pair is (column e, e + 1) along E and (row p, p + 1) along pH, the
+        wrap pair sitting at the last column (row).  Ratios are NaN where
+        nothing was attempted."""
+        n_E, n_pH = int(self.st.n_E), int(self.st.n_pH)
+        c = self.ex_count.cpu().numpy()
+        out = {}
+        for d, name in ((0, "E"), (1, "pH")):
+            att = c[d, 0].reshape(n_pH, n_E)
+            acc = c[d, 1].reshape(n_pH, n_E)
+            with np.errstate(invalid="ignore", divide="ignore"):
+                ratio = np.where(att > 0, acc / np.maximum(att, 1), np.nan)
+            out[name] = {"attempts": att, "accepted": acc, "ratio": ratio}
+        return out
+
+    def metrics(self) -> dict:
+        """One record of the run's observables at the current step (host
+        values, JSON-serialisable): step and exchange attempt, per replica its
+        E, pH, energies (GB, Coulomb, soft repulsion) and the states of its
+        sites, the exchange grid, and the exchange counters."""
+        import torch
+        E_tot = self.energies()
+        torch.cuda.synchronize(self.xyzq.device)
+        M = self.ctx.M
+        rec = {"step": self.step, "attempt": int(self.st.attempt),
+               "E": self.E.cpu().tolist(), "pH": self.pH.cpu().tolist(),
+               "energies": E_tot.cpu().tolist(), "grid": self.grid.cpu().tolist(),
+               "ex_attempts": self.ex_count[:, 0].cpu().tolist(),
+               "ex_accepted": self.ex_count[:, 1].cpu().tolist()}
+        if self.sites is not None:
+            off = self.sites.site_off_host
+            st = self.state.cpu().numpy()
+            rec["states"] = [st[off[r]:off[r + 1]].tolist() for r in range(M)]
+        return rec
+
+    def log_metrics(self, path: str) -> dict:
+        """Appends metrics() to a JSON-lines file and returns the record."""
+        import json
+        rec = self.metrics()
+        with open(path, "a") as f:
+            f.write(json.dumps(rec) + "\n")
+        return rec
 
 
 def save_checkpoint(path: str, ck: dict) -> None:

@@ -813,6 +813,7 @@ int enqueue_exchange(gb_ctx* c, gb_md_state* st, const gb_sites* sites, cudaStre
     x.state = st->state;
     x.ctr = c->ctr;
     x.err = c->err;
+    x.ex_count = (gbk::u64*)st->ex_count;
     x.ex_dim = st->ex_dim;
     x.wrap = st->wrap;
     x.seed = st->seed;
@@ -1146,7 +1147,8 @@ extern "C" int gb_autotune_md(gb_ctx* c, gb_md_state* st, const gb_sites* sites,
     const Buf bufs[] = {{(void*)st->xyzq, 16 * N}, {(void*)st->vel, 16 * N}, {(void*)st->force, 16 * N},
                         {(void*)st->R, 4 * N},     {(void*)st->state, 4 * n_sites},
                         {(void*)st->pH, st->pH ? 8 * M : 0}, {(void*)st->E, st->E ? 8 * M : 0},
-                        {(void*)st->grid, st->grid ? 4 * M : 0}};
+                        {(void*)st->grid, st->grid ? 4 * M : 0},
+                        {(void*)st->ex_count, st->ex_count ? 32 * M : 0}};
     size_t total = 0;
     for (const Buf& b : bufs) total += (b.p ? b.bytes : 0);
     unsigned char* save = nullptr;

@@ -664,6 +664,12 @@ __global__ void k_grid_exchange(GridExArgs A) {
     const Philox4 w = philox4x64((u64)(l * len + a), attempt, 3, 0, A.seed, 0);
     const int acc = (delta <= 0.0) || (unif53(w.w[0]) < exp(-delta));
     if (acc) { *pa = j; *pb = i; }
+    if (A.ex_count) {
+        const int ng = A.n_pH * A.n_E;
+        u64* cnt = A.ex_count + (size_t)(dimE ? 0 : 2) * ng + (l * ladder_stride + a * slot_stride);
+        atomicAdd(cnt, 1ull);
+        if (acc) atomicAdd(cnt + ng, 1ull);
+    }
     double* vr = dimE ? A.E_rep : A.pH_rep;
     vr[*pa] = values[a];
     vr[*pb] = values[b];

@@ -227,6 +227,7 @@ struct GridExArgs {
     const int32_t* state;
     const u64* ctr;
     int* err;                  // GB_ERR_INVALID_ARG on a state outside its site's range
+    u64* ex_count;             // nullable [2 dims][attempts, acceptances][n_pH * n_E]
     int32_t ex_dim;            // 0 E only, 1 pH only, 2 alternate
     int32_t wrap;
     u64 seed;

@@ -49,7 +49,8 @@ def _sim(pkg, b, t, lad, mc_mode):
 def test_resumed_run_equals_the_uninterrupted_one(pkg, tmp_path, mc_mode):
     """40 steps in one simulation against 20 steps, a checkpoint written to a
     file, a fresh simulation restored from it and 20 more steps: coordinates,
-    charges, velocities, site states, exchange grid and E identical."""
+    charges, velocities, site states, exchange grid, E and the exchange
+    counters identical."""
     import torch
     device()
     b = synth.random_batch([300, 150, 220, 96], seed=41)
@@ -65,7 +66,7 @@ def test_resumed_run_equals_the_uninterrupted_one(pkg, tmp_path, mc_mode):
     c = _sim(pkg, b, t, lad, mc_mode).restore(pkg.load_checkpoint(p)).run(20)
     c.sync()
     assert c.step == a.step == 40
-    for k in ("xyzq", "vel", "state", "grid", "E", "pH"):
+    for k in ("xyzq", "vel", "state", "grid", "E", "pH", "ex_count"):
         assert torch.equal(getattr(a, k), getattr(c, k)), k
     assert int(c.st.attempt) == int(a.st.attempt) == 4
     # the run moved: exchanges and MC did something
