@@ -177,7 +177,9 @@ int gb_energy_forces(gb_ctx* ctx, const float* xyzq, const float* rad_screen, fl
 typedef struct {
     int32_t n_rep;
     int32_t n_sites;
-    const int32_t* site_off_host;   /* HOST int32[M+1] */
+    const int32_t* site_off_host;   /* HOST int32[M+1], the values of site_off: checked
+                                       on the host (0 first, non-decreasing, n_sites
+                                       last; GB_ERR_INVALID_ARG otherwise) */
     const int32_t* site_off;        /* DEVICE copy */
     const int32_t* site_kind;
     const int32_t* site_nstates;

@@ -337,9 +337,22 @@ int ensure_prof_events(gb_ctx* c, int64_t steps) {
 
 bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
+// The replica -> site ranges, checked on the host copy: the kernels walk
+// site_off[r] .. site_off[r+1] and index the per-site tables with it.
+const char* site_off_error(const gb_sites* s) {
+    if (s->n_sites < 0) return "sites->n_sites < 0";
+    if (!s->site_off_host) return "sites->site_off_host is NULL";
+    if (s->site_off_host[0] != 0) return "site_off_host[0] must be 0";
+    for (int r = 0; r < s->n_rep; ++r)
+        if (s->site_off_host[r + 1] < s->site_off_host[r]) return "site_off_host must be non-decreasing";
+    if (s->site_off_host[s->n_rep] != s->n_sites) return "site_off_host[n_rep] must equal n_sites";
+    return nullptr;
+}
+
 int check_sites(gb_ctx* c, const gb_sites* s) {
     if (!s) return fail(c, GB_ERR_INVALID_ARG, "sites is NULL");
     if (s->n_rep != c->M) return fail(c, GB_ERR_INVALID_ARG, "sites->n_rep differs from the context's replica count");
+    if (const char* e = site_off_error(s)) return fail(c, GB_ERR_INVALID_ARG, e);
     if (s->n_sites > 0 && (!s->site_off || !s->site_kind || !s->site_nstates || !s->site_atom_off ||
                            !s->site_atom_idx || !s->site_state_off || !s->site_q_off || !s->q_state ||
                            !s->G_ref || !s->n_H || !s->n_e || !s->pKa_ref || !s->E0_ref))
@@ -702,6 +715,8 @@ extern "C" int eremd_exchange(int32_t n_ladders, int32_t len, int32_t ladder_str
 extern "C" int gb_count_bound(const gb_sites* s, const int32_t* state, int32_t kind,
                               int32_t* out, void* stream) {
     if (!s || !state || !out || !s->site_off) return fail(nullptr, GB_ERR_INVALID_ARG, "NULL argument");
+    if (s->n_rep < 1) return fail(nullptr, GB_ERR_INVALID_ARG, "sites->n_rep must be >= 1");
+    if (const char* e = site_off_error(s)) return fail(nullptr, GB_ERR_INVALID_ARG, e);
     if (s->n_sites > 0 && (!s->site_kind || !s->site_nstates || !s->site_state_off || !s->n_H || !s->n_e))
         return fail(nullptr, GB_ERR_INVALID_ARG, "a site table pointer is NULL");
     cudaError_t e = gbk::launch_count(s->site_off, s->site_kind, s->site_nstates, s->site_state_off, s->n_H, s->n_e,

@@ -57,3 +57,25 @@ def test_create_without_gpu_fails_cleanly(lib):
         pytest.skip("a GPU is present")
     with pytest.raises(pkg.GBError):
         pkg.Context([0, 10])
+
+
+@pytest.mark.parametrize("off,n_sites,msg", [
+    ([1, 2, 3], 3, "site_off_host\\[0\\]"),
+    ([0, 3, 2], 2, "non-decreasing"),
+    ([0, 2, 4], 5, "must equal n_sites"),
+    (None, 4, "site_off_host is NULL"),
+])
+def test_site_offsets_are_checked_on_the_host(lib, off, n_sites, msg):
+    """gb_count_bound rejects a malformed replica -> site table before any
+    CUDA call (the device pointers given here are never dereferenced)."""
+    pkg.load()
+    s = pkg.Sites()
+    s.n_rep, s.n_sites = 2, n_sites
+    arr = (ctypes.c_int32 * 3)(*off) if off is not None else None
+    s.site_off_host = ctypes.cast(arr, ctypes.c_void_p) if arr is not None else None
+    fake = 256                               # any non-NULL device address
+    for k in ("site_off", "site_kind", "site_nstates", "site_state_off", "n_H", "n_e"):
+        setattr(s, k, fake)
+    rc = pkg.load().gb_count_bound(ctypes.byref(s), fake, 1, fake, None)
+    assert rc == -1
+    assert re.search(msg, pkg.load().gb_last_error(None).decode())
