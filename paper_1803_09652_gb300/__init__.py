@@ -465,16 +465,7 @@ class Simulation:
         pair is (column e, e + 1) along E and (row p, p + 1) along pH, the
         wrap pair sitting at the last column (row).  Ratios are NaN where
         nothing was attempted."""
-        n_E, n_pH = int(self.st.n_E), int(self.st.n_pH)
-        c = self.ex_count.cpu().numpy()
-        out = {}
-        for d, name in ((0, "E"), (1, "pH")):
-            att = c[d, 0].reshape(n_pH, n_E)
-            acc = c[d, 1].reshape(n_pH, n_E)
-            with np.errstate(invalid="ignore", divide="ignore"):
-                ratio = np.where(att > 0, acc / np.maximum(att, 1), np.nan)
-            out[name] = {"attempts": att, "accepted": acc, "ratio": ratio}
-        return out
+        return exchange_ratios(self.ex_count.cpu().numpy(), int(self.st.n_pH), int(self.st.n_E))
 
     def metrics(self) -> dict:
         """One record of the run's observables at the current step (host
@@ -503,6 +494,22 @@ class Simulation:
         with open(path, "a") as f:
             f.write(json.dumps(rec) + "\n")
         return rec
+
+
+def exchange_ratios(ex_count, n_pH: int, n_E: int) -> dict:
+    """Host view of gb_md_state.ex_count (int64 [2][2][n_pH * n_E]): for
+    "E" (direction 0) and "pH" (direction 1) the attempts, acceptances and
+    acceptance ratio (NaN where nothing was attempted) of every neighbour
+    pair, as [n_pH, n_E] arrays indexed by the pair's first slot."""
+    c = np.asarray(ex_count).reshape(2, 2, n_pH * n_E)
+    out = {}
+    for d, name in ((0, "E"), (1, "pH")):
+        att = c[d, 0].reshape(n_pH, n_E)
+        acc = c[d, 1].reshape(n_pH, n_E)
+        ratio = np.full(att.shape, np.nan)
+        np.divide(acc, att, out=ratio, where=att > 0)
+        out[name] = {"attempts": att, "accepted": acc, "ratio": ratio}
+    return out
 
 
 def save_checkpoint(path: str, ck: dict) -> None:

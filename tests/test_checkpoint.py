@@ -84,3 +84,22 @@ def test_restore_rejects_a_checkpoint_of_another_layout(pkg):
     t2 = b2.site_tables(oracle.site_reference_energies(b2, oracle_params()))
     with pytest.raises(ValueError, match="xyzq"):
         _sim(pkg, b2, t2, lad, 0).restore(ck)
+
+
+def test_exchange_ratios_of_the_counters():
+    """The host view of the exchange counters: per direction, attempts and
+    acceptances in [n_pH, n_E] by first slot, ratios NaN where nothing was
+    attempted."""
+    import paper_1803_09652_gb300 as pkg
+    n_pH, n_E = 2, 3
+    c = np.zeros((2, 2, n_pH * n_E), np.int64)
+    c[0, 0, [0, 1, 3]] = [10, 4, 8]          # E pairs: (0,0)-(0,1), (0,1)-(0,2), (1,0)-(1,1)
+    c[0, 1, [0, 1, 3]] = [5, 4, 0]
+    c[1, 0, 2] = 6                            # pH pair: (0,2)-(1,2)
+    c[1, 1, 2] = 3
+    st = pkg.exchange_ratios(c, n_pH, n_E)
+    assert st["E"]["attempts"].shape == (n_pH, n_E)
+    assert st["E"]["ratio"][0, 0] == 0.5 and st["E"]["ratio"][0, 1] == 1.0 and st["E"]["ratio"][1, 0] == 0.0
+    assert np.isnan(st["E"]["ratio"][0, 2]) and np.isnan(st["E"]["ratio"][1, 2])
+    assert st["pH"]["ratio"][0, 2] == 0.5 and np.isnan(st["pH"]["ratio"]).sum() == 5
+    assert st["pH"]["accepted"].sum() == 3 and st["E"]["attempts"].sum() == 22
