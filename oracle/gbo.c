@@ -179,22 +179,11 @@ double gbo_hct_pair_dr_cut(double r, double a, double s, double rc) {
     return d;
 }
 
-/* The pair-cutoff decision is a yes/no taken by floating point, and the
- * method fixes no precision for it: it is taken in single precision, as the
- * GPU path takes it, so that both count the same pairs.  Coordinates rounded
- * to float, d = x_j - x_i per axis, r^2 = fma(dx, dx, fma(dy, dy, dz * dz)),
- * compared with the float square of the float cutoff; everything else about
- * the pair stays in double precision. */
-static int beyond_cut(const double* x, int64_t i, int64_t j, const gbo_params* p) {
-    if (!(p->cut > 0.0)) return 0;
-    const float dx = (float)x[3 * j] - (float)x[3 * i];
-    const float dy = (float)x[3 * j + 1] - (float)x[3 * i + 1];
-    const float dz = (float)x[3 * j + 2] - (float)x[3 * i + 2];
-    const float dz2 = dz * dz;
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz2));
-    const float c = (float)p->cut;
-    const float c2 = c * c;
-    return r2 > c2;
+/* Pair cutoff of the GB and Coulomb sums: a pair farther apart than `cut`
+ * (exact distance, double precision) contributes nothing; cut <= 0 means no
+ * cutoff. */
+static int beyond_cut(double r, const gbo_params* p) {
+    return p->cut > 0.0 && r > p->cut;
 }
 
 static double dist(const double* x, int64_t i, int64_t j, double d[3]) {
@@ -282,8 +271,8 @@ static double gb_dg(double f, const gbo_params* p) {
  *   E_GB   = -1/2 k_e sum_i sum_j q_i q_j g(f_ij)   (f_ii = R_i; g above: 
  *            (1/eps_in - 1/eps_out) / f without salt)
  *   E_Coul = (k_e / eps_in) sum_{i<j} q_i q_j / r_ij
- * pairs with r_ij > cut are left out when cut > 0 (truncation, decided by
- * beyond_cut); self terms are kept.  E[0] = E_GB, E[1] = E_Coul. */
+ * pairs with r_ij > cut are left out when cut > 0 (truncation); self terms
+ * are kept.  E[0] = E_GB, E[1] = E_Coul. */
 void gbo_energy_fixed_radii(int64_t n, const double* x, const double* q, const double* R,
                             const gbo_params* p, double E[2]) {
     double egb = 0.0, ecoul = 0.0;
@@ -295,7 +284,7 @@ void gbo_energy_fixed_radii(int64_t n, const double* x, const double* q, const d
             }
             double d[3];
             double r = dist(x, i, j, d);
-            if (beyond_cut(x, i, j, p)) continue;          /* pair cutoff: truncated */
+            if (beyond_cut(r, p)) continue;                /* pair cutoff: truncated */
             egb += -0.5 * GBO_KE * q[i] * q[j] * gb_g(f_gb(r, R[i], R[j]), p);
             if (j > i) ecoul += (GBO_KE / p->eps_in) * q[i] * q[j] / r;
         }
@@ -328,7 +317,7 @@ void gbo_energy_forces(int64_t n, const double* x, const double* q, const double
             if (j == i) continue;
             double d[3];
             double r = dist(x, i, j, d);
-            if (beyond_cut(x, i, j, p)) continue;          /* pair cutoff: truncated */
+            if (beyond_cut(r, p)) continue;                /* pair cutoff: truncated */
             double RR = R[i] * R[j];
             double D = r * r / (4.0 * RR);
             double e = exp(-D);

@@ -47,3 +47,48 @@ def energy_rel_err(E_gpu, E_ref):
     tot_g = E_gpu[:, 0] + E_gpu[:, 1]
     tot_r = E_ref[:, 0] + E_ref[:, 1]
     return np.abs(tot_g - tot_r) / np.maximum(np.abs(tot_r), 1e-30)
+
+
+# Pair cutoff.  The library decides whether a pair lies within `cut` from its
+# FP32 squared distance; the oracle from the exact distance.  Rounding of the
+# FP32 differences and of r^2 moves r by a few float ulps (one ulp of r is
+# about 1.2e-7 r), so the two decisions can differ only for pairs with
+# |r - cut| <= CUT_BAND * cut (about 8 ulps).  Each such pair moves the
+# energy by up to kcal/mol.  The parity tests therefore list the pairs in
+# that band, and take a cutoff (within a few 1e-4 A of the one they ask for)
+# whose band is empty: on their inputs both sides count the same pairs.
+CUT_BAND = 1e-6
+
+
+def pairs_near_cut(xyz_list, cut, band=None):
+    """Number of pairs, over the given coordinate sets (each (n, 3), any
+    float type, taken as exact doubles), whose distance lies within `band`
+    of `cut` (default CUT_BAND * cut)."""
+    band = CUT_BAND * cut if band is None else band
+    count = 0
+    for x in xyz_list:
+        x = np.asarray(x, dtype=np.float64)
+        n = len(x)
+        for a in range(0, n, 1024):
+            d = np.sqrt(((x[a:a + 1024, None, :] - x[None, :, :]) ** 2).sum(-1))
+            i, j = np.nonzero(np.abs(d - cut) <= band)
+            count += int(np.count_nonzero(j > i + a))
+    return count
+
+
+def batch_xyz(b):
+    """Coordinates of every replica of a synth.Batch, one array each."""
+    x = b.xyzq()[:, :3]
+    return [x[b.atom_off[r]:b.atom_off[r + 1]] for r in range(b.n_rep)]
+
+
+def clear_cut(xyz_list, near, band=None, tries=200):
+    """The float32 value closest to `near` on a 1e-4 A grid (near, near +
+    1e-4, near - 1e-4, ...) with no pair of the coordinate sets within the
+    band of it."""
+    for k in range(tries):
+        step = (k + 1) // 2 * (1 if k % 2 else -1)
+        c = f32(near + 1e-4 * step)
+        if pairs_near_cut(xyz_list, c, band) == 0:
+            return c
+    raise AssertionError(f"no cutoff near {near} leaves the band empty")

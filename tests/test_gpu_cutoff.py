@@ -5,7 +5,12 @@ the molecule; batches with empty replicas), the Monte Carlo energy change and
 the per-residue sweep, one MD step, the allocation-free entry point, cutoffs
 past the molecule bitwise equal to none, and the block neighbour list (a cut
 evaluation of a 100000-atom chain runs in a fraction of the time of the full
-one, with sampled radii and the zero net force still right)."""
+one, with sampled radii and the zero net force still right).
+
+The oracle counts a pair iff its exact distance is within the pair cutoff;
+the library decides from its FP32 r^2.  Each test that compares against the
+oracle with a pair cutoff takes the cutoff nearest the one it names that has
+no pair within the FP32 band of it (gpu_common.CUT_BAND), and asserts so."""
 import ctypes as C
 import time
 
@@ -14,8 +19,8 @@ import pytest
 
 import oracle
 import synth
-from gpu_common import (DG_ABS, E_REL, F_ABS, KT, PHI_ABS, R_REL, device, energy_rel_err, f32,
-                        oracle_params, to_dev)
+from gpu_common import (DG_ABS, E_REL, F_ABS, KT, PHI_ABS, R_REL, batch_xyz, clear_cut, device,
+                        energy_rel_err, f32, oracle_params, pairs_near_cut, to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -76,6 +81,9 @@ def _check(out, ref, bar):
 ])
 def test_cutoff_energy_forces_match_oracle(pkg, rgbmax, cut, kappa):
     b = synth.random_batch([2100, 300, 64, 33, 1], seed=41)
+    if cut:
+        cut = clear_cut(batch_xyz(b), cut)
+        assert pairs_near_cut(batch_xyz(b), cut) == 0
     out = _run(pkg, b, rgbmax=rgbmax, cut=cut, kappa=kappa)
     p = oracle_params(rgbmax=f32(rgbmax), cut=f32(cut), kappa=f32(kappa))
     ref = oracle.batch_energy_forces(b, p, with_phi=True)
@@ -86,8 +94,10 @@ def test_cutoff_batch_with_empty_replicas(pkg):
     """Empty replicas before, between and after the others: the list builder's
     replica search and the lists' runs stay inside each replica."""
     b = synth.random_batch([0, 700, 0, 33, 1, 1200, 0], seed=47)
-    out = _run(pkg, b, rgbmax=8.0, cut=9.0)
-    p = oracle_params(rgbmax=8.0, cut=9.0)
+    cut = clear_cut(batch_xyz(b), 9.0)
+    assert pairs_near_cut(batch_xyz(b), cut) == 0
+    out = _run(pkg, b, rgbmax=8.0, cut=cut)
+    p = oracle_params(rgbmax=8.0, cut=cut)
     ref = oracle.batch_energy_forces(b, p, with_phi=True)
     _check(out, ref, born_bar(b, p))
 
@@ -97,13 +107,14 @@ def test_cutoff_sweep_matches_oracle(pkg):
     cutoff in the site rows and the site-site block."""
     import torch
     dev = device()
-    rgbmax, cut = 10.0, 7.0
-    p = oracle_params(rgbmax=f32(rgbmax), cut=f32(cut))
     reps = [synth.make_replica(n, 90 + k, specs) for k, (n, specs) in enumerate([
         (400, [(1, 8, 2), (0, 6, 4), (0, 9, 3), (0, 5, 2), (1, 12, 2)]),
         (150, [(0, 12, 3), (1, 6, 2)]),
     ])]
     b = synth.Batch(reps, pH=np.array([4.4, 4.9]), E=synth.E0_REF_V + np.array([0.0, 0.03]))
+    rgbmax, cut = 10.0, clear_cut(batch_xyz(b), 7.0)
+    assert pairs_near_cut(batch_xyz(b), cut) == 0
+    p = oracle_params(rgbmax=f32(rgbmax), cut=f32(cut))
     G = np.concatenate([oracle.site_reference_energies(synth.Batch([r], pH=b.pH[k:k + 1], E=b.E[k:k + 1]), p)
                         for k, r in enumerate(b.replicas)])
     t = b.site_tables(G)
@@ -149,9 +160,10 @@ def test_cutoffs_past_the_molecule_are_the_uncut_path(pkg):
 def test_cutoff_mc_energy_change_matches_oracle(pkg):
     import torch
     dev = device()
-    rgbmax, cut = 10.0, 8.0
-    p = oracle_params(rgbmax=f32(rgbmax), cut=f32(cut))
     b = synth.config_plain()
+    rgbmax, cut = 10.0, clear_cut(batch_xyz(b), 8.0)
+    assert pairs_near_cut(batch_xyz(b), cut) == 0
+    p = oracle_params(rgbmax=f32(rgbmax), cut=f32(cut))
     G = oracle.site_reference_energies(b, p)
     t = b.site_tables(G)
     xyzq, rad = to_dev(b, dev)
@@ -182,8 +194,25 @@ def test_cutoff_md_step_matches_oracle(pkg):
     import torch
     dev = device()
     b = synth.random_batch([400, 120, 33], seed=43, sites=False)
-    params = pkg.default_params(rep_k=100.0, rep_sigma=2.5, rgbmax=9.0, cut=8.0)
-    p = oracle_params(rep_k=100.0, rep_sigma=2.5, rgbmax=9.0, cut=8.0)
+    x, q, rho, scr, off = oracle.batch_arrays(b)
+    # the forces are compared at the start (same coordinates on both sides)
+    # and after the step, where the two sides' coordinates differ by up to
+    # 1e-5 A per atom: the cutoff must leave both bands empty
+    cut, near = None, 8.0
+    for _ in range(40):
+        c = clear_cut(batch_xyz(b), near)
+        pc = oracle_params(rep_k=100.0, rep_sigma=2.5, rgbmax=9.0, cut=c)
+        Fc, _ = oracle.forces_all(off, x, q, rho, scr, pc)
+        xc, vc = x.copy(), np.zeros_like(x)
+        oracle.md_step(off, xc, vc, q, rho, scr, Fc, 5, 1, pc)
+        moved = [xc[off[r]:off[r + 1]] for r in range(b.n_rep)]
+        if pairs_near_cut(moved, c, band=1e-6 * c + 2e-5) == 0:
+            cut = c
+            break
+        near = c + 2e-4
+    assert cut is not None
+    params = pkg.default_params(rep_k=100.0, rep_sigma=2.5, rgbmax=9.0, cut=cut)
+    p = oracle_params(rep_k=100.0, rep_sigma=2.5, rgbmax=9.0, cut=cut)
     ctx = pkg.Context(b.atom_off, params)
     N, M = b.n_atoms, b.n_rep
     S = dict(xyzq=torch.as_tensor(b.xyzq(), device=dev), rad=torch.as_tensor(b.rad_screen(), device=dev),
@@ -202,7 +231,6 @@ def test_cutoff_md_step_matches_oracle(pkg):
     st.mc_every, st.ex_every, st.ex_dim, st.wrap = 0, 0, 0, 1
     ctx.md_init(st)
     torch.cuda.synchronize()
-    x, q, rho, scr, off = oracle.batch_arrays(b)
     F0, _ = oracle.forces_all(off, x, q, rho, scr, p)
     assert np.abs(S["force"][:, :3].cpu().numpy() - F0).max() <= F_ABS
     ctx.md_segment(st, None, 1)
@@ -225,8 +253,10 @@ def test_cutoff_static_entry_matches_oracle(pkg):
     f.restype = C.c_int
     b = synth.random_batch([1500], seed=44)
     n = b.n_atoms
+    cut = clear_cut(batch_xyz(b), 9.0)
+    assert pairs_near_cut(batch_xyz(b), cut) == 0
     xyzq, rad = to_dev(b, dev)
-    params = pkg.default_params(rgbmax=8.0, cut=9.0)
+    params = pkg.default_params(rgbmax=8.0, cut=cut)
     out = dict(R=torch.empty(n, dtype=torch.float32, device=dev),
                F=torch.empty((n, 3), dtype=torch.float32, device=dev),
                F_fixed=torch.zeros((3, n), dtype=torch.int64, device=dev),
@@ -238,7 +268,7 @@ def test_cutoff_static_entry_matches_oracle(pkg):
     assert rc == 0
     torch.cuda.synchronize()
     o = {k: v.cpu().numpy() for k, v in out.items()}
-    p = oracle_params(rgbmax=8.0, cut=9.0)
+    p = oracle_params(rgbmax=8.0, cut=cut)
     ref = oracle.batch_energy_forces(b, p, with_phi=True)
     _check(o, ref, born_bar(b, p))
 

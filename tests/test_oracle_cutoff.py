@@ -90,8 +90,9 @@ def test_large_cutoffs_change_nothing(orc, mol):
 
 def cut_in_gap(x, near):
     """A cutoff near `near` in the middle of the widest gap between pair
-    distances there, so that single- and double-precision comparisons of
-    every pair with it agree."""
+    distances there: the truncated energy jumps where a pair crosses the
+    cutoff, so finite differences (and numpy's own distances, which may round
+    differently from the oracle's) need every pair well away from it."""
     d = np.linalg.norm(x[:, None] - x[None], axis=2)[np.triu_indices(len(x), 1)]
     d = np.sort(d[np.abs(d - near) < 0.2])
     k = int(np.argmax(np.diff(d)))
@@ -120,25 +121,27 @@ def test_pair_cutoff_drops_exactly_the_far_pairs(orc, mol):
     assert E_cut == pytest.approx(E_all - far, rel=1e-11, abs=1e-9)
 
 
-def test_pair_cutoff_decision_is_single_precision(orc):
-    """Two atoms straddling the cutoff by less than an FP32 ulp of r^2: the
-    pair counts exactly when its float32 r^2 is within the float32 cut^2."""
+def test_pair_cutoff_boundary_is_the_exact_distance(orc):
+    """Two ions on either side of the cutoff, within 1e-12 relative of it: on
+    the inside the truncated energy equals the untruncated one, on the
+    outside it equals the two isolated ions' Born energies (one-atom
+    evaluations).  The decision is taken on the exact distance, however close
+    the pair lies to the cutoff."""
     cut = 10.0
-    for dx in (10.0, 10.0 + 1e-7, 10.0 + 4e-7, 10.0 + 6e-7, 10.0 - 4e-7,
-               np.nextafter(np.float32(10.0), np.float32(11.0)),
-               np.nextafter(np.float32(10.0), np.float32(9.0))):
-        x = np.array([[0.0, 0.0, 0.0], [float(dx), 0.0, 0.0]])
-        q = np.array([0.5, -0.5])
-        R = np.array([1.5, 1.5])
+    q = np.array([0.5, -0.5])
+    R = np.array([1.5, 1.7])
+    iso = (orc.energy_fixed_radii(np.zeros((1, 3)), q[:1], R[:1]).sum()
+           + orc.energy_fixed_radii(np.zeros((1, 3)), q[1:], R[1:]).sum())
+    for dx, inside in ((cut * (1 - 1e-12), True), (cut, True), (cut * (1 + 1e-12), False),
+                       (cut + 1e-7, False), (cut - 1e-7, True)):
+        x = np.array([[0.0, 0.0, 0.0], [dx, 0.0, 0.0]])
         E = orc.energy_fixed_radii(x, q, R, orc.default_params(cut=cut))
-        r2 = np.float32(dx) * np.float32(dx)
-        inside = r2 <= np.float32(np.float32(cut) * np.float32(cut))
-        assert (E[1] != 0.0) == bool(inside), dx
-    # 10 + 1e-7 is beyond the cutoff in double precision but rounds to 10 in
-    # float: counted
-    x = np.array([[0.0, 0.0, 0.0], [10.0 + 1e-7, 0.0, 0.0]])
-    assert orc.energy_fixed_radii(x, np.array([0.5, -0.5]), np.array([1.5, 1.5]),
-                                  orc.default_params(cut=cut))[1] != 0.0
+        if inside:
+            assert E.sum() == pytest.approx(orc.energy_fixed_radii(x, q, R).sum(), rel=1e-14), dx
+            assert E[1] != 0.0
+        else:
+            assert E.sum() == pytest.approx(iso, rel=1e-14), dx
+            assert E[1] == 0.0
 
 
 def test_forces_fd_with_both_cutoffs(orc, mol):
