@@ -341,21 +341,29 @@ int gb_autotune_md(gb_ctx* ctx, gb_md_state* state, const gb_sites* sites, int64
  * of device memory that the library declares statically (about 0.7 MB, held by
  * every GPU that loads the library until the process exits).
  *
- * Same inputs, outputs and arithmetic as gb_energy_forces for a batch of one
- * replica of n_atoms atoms (1 <= n_atoms <= GB_STATIC_MAX_ATOMS); E_out is
- * double[3]; the cutoffs of gb_params apply pair by pair (no block is
- * skipped: this path builds no bounding boxes).  Works on the current
- * device.  It allocates nothing: no
- * cudaMalloc, no cudaFree, no allocating library routine.
- *  - The first call on a device looks up the array's device address (once per
- *    device); make that first call before any stream capture.
+ * Same inputs and outputs as gb_energy_forces for a batch of one replica of
+ * n_atoms atoms (1 <= n_atoms <= GB_STATIC_MAX_ATOMS); E_out is double[3].
+ * The arithmetic differs in one respect: this path builds no tile bounding
+ * boxes, so no block is proven far and every block takes the exact
+ * near-field path (with cutoffs, every block is tested pair by pair and none
+ * is skipped).  Results therefore agree with gb_energy_forces within the
+ * parity tolerances (energy 1e-6 relative, forces 1e-3 kcal/mol/A), not bit
+ * for bit, and the call is slower than a context's.  Works on the current
+ * device.  It allocates nothing: no cudaMalloc, no cudaFree, no allocating
+ * library routine.
+ *  - A call outside stream capture looks up the array's device address with
+ *    the device current (this allocates nothing).  A call on a capturing
+ *    stream reuses the address of the last call on that device outside
+ *    capture, so make one call outside capture first (again after a
+ *    cudaDeviceReset); otherwise it returns GB_ERR_INVALID_ARG.
  *  - Every call on a device shares the one array and clears its accumulators
  *    first; calls that overlap on the GPU (other streams, other host threads)
  *    race on it and must be serialised by the caller.
  *  - Returns GB_ERR_INVALID_ARG when n_atoms is outside 1..GB_STATIC_MAX_ATOMS
  *    or an argument is NULL / misaligned, GB_ERR_CUDA on a launch error.
  *    Device-side non-finite results are not reported (there is no context to
- *    hold the error word); they show up as NaN in the outputs. */
+ *    hold the error word, so GB_ERR_NONFINITE never comes back); they show up
+ *    as NaN in the outputs. */
 #define GB_STATIC_MAX_ATOMS 8192
 int gb_energy_forces_static(int32_t n_atoms, const gb_params* params, const float* xyzq,
                             const float* rad_screen, float* R_out, int64_t* F_fixed,
@@ -375,9 +383,10 @@ int gb_pass_times(gb_ctx* ctx, double* mean_ms);
  * pair passes, the O(N) transforms, replica by replica -- from a queue, each
  * item waiting only for the items of the same replica it depends on, so the
  * passes of different replicas overlap.  A wait that takes too long records
- * GB_ERR_TIMEOUT (see gb_sync_status) instead of hanging.  Disabled: eight
- * launches per step (the kernels gb_energy_forces uses, the BAOAB halves and
- * the tile bounding boxes).  With profiling on, gb_persist_times returns
+ * GB_ERR_TIMEOUT (see gb_sync_status) instead of hanging.  Disabled: six
+ * launches per step (the close-and-open BAOAB step with the tile bounding
+ * boxes, then the three pair passes and their two O(N) transforms), eight
+ * with a cutoff (the neighbour list's reset and build).  With profiling on, gb_persist_times returns
  * out[0] the mean ms per MD step inside the persistent launches of the last
  * block, out[1] the mean ms per launch and out[2] the mean steps per launch. */
 int gb_set_persistent(gb_ctx* ctx, int32_t enable);

@@ -47,21 +47,29 @@ constexpr size_t kBytes = kOffTasks + align256(16ull * kMaxTasks);
 
 __device__ __align__(256) unsigned char gb_static_scratch[kBytes];
 
-// Device address of gb_static_scratch per device ordinal, looked up once per
-// device with that device current (the host-side symbol is only a stand-in).
+// Device address of gb_static_scratch.  The host-side symbol is only a
+// stand-in, so the address is looked up with the device current.  A call
+// outside stream capture looks it up afresh every time: the lookup allocates
+// nothing, and after cudaDeviceReset the module (and with it the array) may
+// come back at another address.  A call on a capturing stream cannot make
+// API calls that might load a module, so it uses the address of the last
+// call on that device outside capture, cached per device ordinal.
 constexpr int kMaxDevices = 64;
 unsigned char* g_scratch[kMaxDevices] = {};
 std::mutex g_scratch_mu;
 
-int scratch_for_current_device(unsigned char** out) {
+int scratch_for_current_device(cudaStream_t s, unsigned char** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GB_ERR_CUDA;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return GB_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, gb_static_scratch) != cudaSuccess || !p) return GB_ERR_CUDA;
         g_scratch[dev] = (unsigned char*)p;
     }
+    if (!g_scratch[dev]) return GB_ERR_INVALID_ARG;   // first call on this device is inside a capture
     *out = g_scratch[dev];
     return GB_OK;
 }
@@ -102,10 +110,10 @@ extern "C" int gb_energy_forces_static(int32_t n_atoms, const gb_params* params,
     if (!R_out && !F_fixed && !F_out && !E_out && !dEdq_out) return GB_ERR_INVALID_ARG;
     if (((uintptr_t)xyzq % 16) || ((uintptr_t)rad_screen % 8)) return GB_ERR_INVALID_ARG;
     if (!gbk::params_ok(*params)) return GB_ERR_INVALID_ARG;
-    unsigned char* base = nullptr;
-    int rc = scratch_for_current_device(&base);
-    if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
+    unsigned char* base = nullptr;
+    int rc = scratch_for_current_device(s, &base);
+    if (rc) return rc;
     const int n = n_atoms;
     const int nb = (n + 31) / 32;
     const int64_t total = gbk::pair_units(n);

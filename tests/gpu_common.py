@@ -92,3 +92,21 @@ def clear_cut(xyz_list, near, band=None, tries=200):
         if pairs_near_cut(xyz_list, c, band) == 0:
             return c
     raise AssertionError(f"no cutoff near {near} leaves the band empty")
+
+
+def oracle_energy_forces_job(args):
+    """Full FP64 oracle evaluation of one molecule: dict(E, F, phi, R).  A
+    module-level function, so that spawned worker processes can run it."""
+    x, q, rho, scr, kw = args
+    o = oracle.energy_forces(x, q, rho, scr, oracle_params(**kw))
+    return {k: o[k] for k in ("E", "F", "phi", "R")}
+
+
+def oracle_pool(n_jobs):
+    """A pool of spawned worker processes for oracle evaluations (spawned, not
+    forked: a child forked from a process that holds a CUDA context can
+    hang), sized to the host's cores."""
+    import multiprocessing as mp
+    import os
+    n = max(2, min(n_jobs, (os.cpu_count() or 2) - 1))
+    return mp.get_context("spawn").Pool(n)

@@ -12,8 +12,9 @@ import ctypes as C
 import numpy as np
 import pytest
 
+import oracle
 import synth
-from gpu_common import E_REL, F_ABS, PHI_ABS, R_REL, device
+from gpu_common import E_REL, F_ABS, PHI_ABS, R_REL, device, energy_rel_err, oracle_params
 
 pytestmark = pytest.mark.gpu
 
@@ -31,14 +32,18 @@ def lib():
     return lib
 
 
-def _static_call(lib, pkg, params, n, xyzq, rad):
+def _outputs(n, dev):
     import torch
-    dev = xyzq.device
-    out = dict(R=torch.full((n,), float("nan"), dtype=torch.float32, device=dev),
+    return dict(R=torch.full((n,), float("nan"), dtype=torch.float32, device=dev),
                F=torch.full((n, 3), float("nan"), dtype=torch.float32, device=dev),
                F_fixed=torch.zeros((3, n), dtype=torch.int64, device=dev),
                E=torch.full((1, 3), float("nan"), dtype=torch.float64, device=dev),
                dEdq=torch.full((n,), float("nan"), dtype=torch.float64, device=dev))
+
+
+def _static_call(lib, pkg, params, n, xyzq, rad, out=None):
+    import torch
+    out = out or _outputs(n, xyzq.device)
     s = torch.cuda.current_stream().cuda_stream
     rc = lib.gb_energy_forces_static(n, C.byref(params), xyzq.data_ptr(), rad.data_ptr(),
                                      out["R"].data_ptr(), out["F_fixed"].data_ptr(),
@@ -94,3 +99,49 @@ def test_static_entry_rejects_sizes_beyond_the_limit(lib):
     rc = lib.gb_energy_forces_static(0, C.byref(params), xyzq.data_ptr(), rad.data_ptr(), R.data_ptr(),
                                      None, None, None, None, s)
     assert rc == -1
+
+
+@pytest.mark.parametrize("n", [8192, 8191, 8129])
+def test_static_entry_at_its_size_limit(lib, n):
+    """At the limit (n = 8192: the largest task list and every sub-buffer of
+    the array full), one atom short of it, and at 8129 atoms (255 tiles, the
+    last holding one atom): two calls in a row against a context, and
+    against the FP64 oracle element by element."""
+    import torch
+    import paper_1803_09652_gb300 as pkg
+    dev = device()
+    params = pkg.default_params()
+    b = synth.Batch([synth.make_replica(n, 60 + n % 7, [])], pH=np.array([7.0]), E=np.array([synth.E0_REF_V]))
+    xyzq = torch.as_tensor(b.xyzq(), device=dev)
+    rad = torch.as_tensor(b.rad_screen(), device=dev)
+    ctx = pkg.Context(b.atom_off, params)
+    ref = {k: v.cpu().numpy() for k, v in ctx.energy_forces(xyzq, rad).items()}
+    ctx.close()
+    for _ in range(2):
+        a = _static_call(lib, pkg, params, n, xyzq, rad)
+        _check(a, ref)
+    x, q, rho, scr, off = oracle.batch_arrays(b)
+    o = oracle.energy_forces(x, q, rho, scr, oracle_params())
+    assert energy_rel_err(a["E"], o["E"][None, :]).max() <= E_REL
+    assert np.abs(a["F"] - o["F"]).max() <= F_ABS
+    assert np.max(np.abs(a["R"] - o["R"]) / o["R"]) <= R_REL
+    assert np.abs(a["dEdq"] - o["phi"]).max() <= PHI_ABS
+
+
+def test_static_entry_allocates_no_device_memory(lib):
+    """Free device memory is the same before and after a warmed-up call (the
+    outputs are allocated beforehand, as such a caller would hold them)."""
+    import torch
+    import paper_1803_09652_gb300 as pkg
+    dev = device()
+    params = pkg.default_params()
+    b = synth.random_batch([4000], seed=33, sites=False)
+    xyzq = torch.as_tensor(b.xyzq(), device=dev)
+    rad = torch.as_tensor(b.rad_screen(), device=dev)
+    out = _outputs(b.n_atoms, dev)
+    _static_call(lib, pkg, params, b.n_atoms, xyzq, rad, out)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    _static_call(lib, pkg, params, b.n_atoms, xyzq, rad, out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
