@@ -11,9 +11,17 @@ __device__ __forceinline__ void set_err(int* err, int code) { atomicCAS(err, 0, 
 
 // --- Born radii: I -> psi -> R (OBC) -------------------------------------------
 // R = 1 / (1/a - tanh(Phi)/rho), Phi = alpha psi - beta psi^2 + gamma psi^3.
-// Written without cancellation: with t = exp(-2|Phi|) and d = rho - a (exact
-// in FP32), 1/a - tanh(Phi)/rho = (d (1 + t) + 2 a t) / (a rho (1 + t)) for
-// Phi >= 0, and 1 - tanh^2 = 4 t / (1 + t)^2.  The integral is read in FP64.
+// Written without cancellation: with t = exp(-2|Phi|),
+//   1/a - tanh(Phi)/rho = (offset (1 + t) + 2 a t) / (a rho (1 + t))   (Phi >= 0)
+// and 1 - tanh^2 = 4 t / (1 + t)^2.  The small difference rho - a enters as
+// the offset itself: taken as rho - fl(rho - offset) it would carry the
+// rounding of a (up to 6e-8 A, 7e-7 of the 0.09 A offset), and since R ->
+// a rho / offset for buried atoms every radius came out low by ~2.4e-7, a
+// bias the self energies of a molecule summed (a 2470-atom replica whose GB
+// and Coulomb energies cancel 14-fold missed the 1e-6 energy bar).  FP32
+// throughout with the accurate expf: the same transform in FP64 met the bar
+// by little more and cost 10 % of an 8 x 2048 MD step on this GPU's FP64
+// units.  The integral is read in FP64.
 // Writes (R, 1/(2R)), the chain prefactor a dR/dpsi, and clears the integral.
 __device__ __forceinline__ void born_finalize_atom(const AtomArgs& A, int64_t g, float* R_out) {
     const float I = (float)((double)(long long)__ldcg(&A.I_acc[g]) * FIX_I_INV);
@@ -21,14 +29,13 @@ __device__ __forceinline__ void born_finalize_atom(const AtomArgs& A, int64_t g,
     const float2 rs = A.rad[g];
     const float rho = rs.x;
     const float a = rho - A.offset;
-    const float d = rho - a;
     const float psi = a * I;
     const float Phi = psi * fmaf(psi, fmaf(A.gamma, psi, -A.beta), A.alpha);
-    const float t = __expf(-2.0f * fabsf(Phi));
+    const float t = expf(-2.0f * fabsf(Phi));
     const float onet = 1.0f + t;
     float R;
     if (Phi >= 0.0f) {
-        R = (a * rho * onet) / fmaf(d, onet, 2.0f * a * t);
+        R = (a * rho * onet) / fmaf(A.offset, onet, 2.0f * a * t);
     } else {  // tanh < 0: 1/a + |tanh|/rho, no cancellation either
         R = 1.0f / (1.0f / a + (1.0f - t) / (onet * rho));
     }
