@@ -1,19 +1,24 @@
 """Benchmark of the GB / C(pH,E)MD / E-REMD hot path on one GB300.
 
-Workload: E-REMD batch of 8 replicas x 2048-atom compact chains (1 redox + 3 pH
-sites), E ladder E0 +- 0.2 V, Langevin 2 fs with GB + Coulomb + chain bonds +
-soft repulsion, MC attempt (protonation then redox) every 10 steps, neighbour
-exchange every 100 steps.  One bench "step" = one exchange period: 100 MD
-steps of every replica, 10 MC rounds, 1 exchange, run through gb_md_segment
-(one CUDA graph replay).
+Default workload: the 2-D C(pH,E) grid, 6 pH x 8 E = 48 replicas of
+25,000-atom compact chains with 40 titratable sites each (8 redox, 32 pH with
+2-4 states), exchanges alternating along E and pH; Langevin 2 fs with GB +
+Coulomb + chain bonds + soft repulsion, MC attempt (protonation then redox)
+every 10 steps, neighbour exchange every 100 steps.  One bench "step" = one
+exchange period: 100 MD steps of every replica, 10 MC rounds, 1 exchange, run
+through gb_md_segment (captured CUDA graphs).  --workload picks one of the
+other configurations (8 x 2048 E-REMD batch, 16 x 4096, uneven 64, a
+100,000-atom chain with cutoffs).
 
 Headline metric: GB pair-interactions/s = sum_r N_r (N_r - 1)/2 per MD step
 x MD steps / device seconds (each MD step evaluates all pairs in three passes).
 Also reported: replica MD-steps/s, the plain form (one context and one launch
 sequence per replica, no graph), the dominant pass's FP32 roofline, an
-end-to-end number through host buffers, and the FP64 oracle on host cores.
+end-to-end number through gb_md_segment_host with the state in pinned host
+memory, and the FP64 oracle on host cores.
 
---impl reference times the FP64 CPU oracle (the reference arm of this build).
+--impl reference times the FP64 CPU oracle (the reference arm of this build)
+on the same workload.
 """
 from __future__ import annotations
 
@@ -33,29 +38,28 @@ import numpy as np  # noqa: E402
 
 MD_PER_STEP = 100          # MD steps per bench step (one exchange period)
 MC_EVERY, EX_EVERY = 10, 100
-N_REP, N_ATOMS = 8, 2048
-SM_COUNT = 152
 FP32_LANES = 128           # FP32 lanes per SM
 # Algorithmic FP32 flops per unordered pair and pass (FMA = 2, add / mul = 1;
 # MUFU ops counted apart), counted on the far-field arithmetic every disjoint
 # pair needs (short polynomials); pairs in near blocks cost more, so these
-# figures are a lower bound of the FP32 work done (derivation in the design doc).
+# figures are a lower bound of the FP32 work done.
 FLOPS_PER_PAIR = {"born": 35.5, "energy": 46.0, "chain": 52.5}
 MUFU_PER_PAIR = {"born": 1, "energy": 3, "chain": 1}
 PASS_NAMES = ["born", "energy", "chain"]
 
 
-WORKLOADS = ("eremd_8x2048", "diff_16x4096", "uneven_64", "grid_48x25000", "cutoff_1x100000")
+WORKLOADS = ("grid_48x25000", "eremd_8x2048", "diff_16x4096", "uneven_64", "cutoff_1x100000")
+DEFAULT_WORKLOAD = "grid_48x25000"
 # GB with cutoffs: Born-radius cutoff and pair cutoff (A) of the cutoff workload
 CUTOFFS = {"cutoff_1x100000": dict(rgbmax=12.0, cut=12.0)}
 
 
-def workload(name="eremd_8x2048"):
-    """The batch of a named configuration (the headline is the E-REMD batch;
-    the others are the parity-test configurations, benched on request)."""
+def workload(name=DEFAULT_WORKLOAD):
+    """The batch of a named configuration (the headline is the 2-D grid, the
+    largest single-GPU configuration; the others are benched on request)."""
     import synth
     if name == "eremd_8x2048":
-        return synth.config_eremd(N_REP, N_ATOMS, seed=0)
+        return synth.config_eremd(8, 2048, seed=0)
     if name == "diff_16x4096":
         return synth.config_diff(16, 4096)
     if name == "uneven_64":
@@ -65,6 +69,21 @@ def workload(name="eremd_8x2048"):
     if name == "cutoff_1x100000":
         return synth.config_cutoff(100000)
     raise ValueError(name)
+
+
+def est_md_step_s(b):
+    """Rough seconds per MD step of the batched form (about 2.5e11 pair
+    interactions/s), used only to size the untimed and auxiliary regions."""
+    return max(b.pairs_per_eval(), 1) / 2.5e11
+
+
+def bench_config(name, b, pairs_md):
+    """The workload as both arms report it (identical dicts)."""
+    return {"workload": name, "replicas": b.n_rep, "atoms_total": b.n_atoms,
+            "md_steps_per_step": MD_PER_STEP, "mc_every": MC_EVERY, "exchange_every": EX_EVERY,
+            "pairs_per_md_step": pairs_md, "cutoffs_A": CUTOFFS.get(name),
+            "pairs_counted": "within the pair cutoff at the start" if name in CUTOFFS else "all pairs",
+            "l2": "flushed between GPU steps (256 MB write)", "parallelism": "replicas"}
 
 
 def pairs_per_md_step(b, name):
@@ -125,48 +144,53 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------------
 def _oracle_md_worker(job):
-    """One host process: the FP64 oracle's force evaluation + BAOAB step of one
-    2048-atom replica of the workload, repeated for `seconds` (at least
-    `min_steps` steps).  Returns (MD steps, seconds)."""
-    seconds, min_steps, seed = job
+    """One host process: the FP64 oracle's BAOAB MD step (force evaluation of
+    GB + Coulomb + restraints, then the update) of replica 0 of the workload,
+    n_steps times.  First, untimed: the forces at the starting coordinates and
+    `warm` MD steps (the process's warm-up).  Returns (MD steps, timed
+    seconds, pair interactions per MD step)."""
+    name, n_steps, warm, seed = job
     import oracle
     import synth
     oracle.build()
-    b = workload()
-    one = b.replicas[0]
-    sb = synth.Batch([one], pH=b.pH[:1], E=b.E[:1])
+    b = workload(name)
+    sb = synth.Batch([b.replicas[0]], pH=b.pH[:1], E=b.E[:1])
     x, q, rho, scr, off = oracle.batch_arrays(sb)
     v = np.zeros_like(x)
-    p = oracle.default_params()
+    p = oracle.default_params(rep_k=100.0, rep_sigma=2.5, **CUTOFFS.get(name, {}))
     F, _ = oracle.forces_all(off, x, q, rho, scr, p)
-    n = 0
+    for k in range(warm):
+        oracle.md_step(off, x, v, q, rho, scr, F, seed, k + 1, p)
     t0 = time.perf_counter()
-    while time.perf_counter() - t0 < seconds or n < min_steps:
-        oracle.md_step(off, x, v, q, rho, scr, F, seed, n + 1, p)
-        n += 1
-    return n, time.perf_counter() - t0
+    for k in range(warm, warm + n_steps):
+        oracle.md_step(off, x, v, q, rho, scr, F, seed, k + 1, p)
+    pairs = pairs_per_md_step(sb, name)
+    return n_steps, time.perf_counter() - t0, pairs
 
 
-def oracle_throughput(procs, seconds=0.0, min_steps=1):
-    """The oracle as it stands on `procs` host cores: one independent replica
-    per process (replicas are independent between exchanges), processes
-    started with spawn.  Returns (pair-interactions/s, MD steps, wall s)."""
+def oracle_throughput(name, n_steps, procs, warmup=0):
+    """The oracle as it stands on host cores: n_steps MD steps of one replica
+    of the workload (replicas are independent between exchanges), spread over
+    `procs` spawned processes, one per core.  Each process first computes its
+    starting forces (one force evaluation, untimed); when there are fewer
+    processes than `warmup` steps, each also runs untimed MD steps until the
+    processes' warm-up covers them.  The job's time is the slowest process's
+    timed region (as the slowest rank's time on GPUs).  Returns
+    (pair-interactions/s, MD steps, seconds, processes)."""
     import oracle
     oracle.build()
-    pairs = N_ATOMS * (N_ATOMS - 1) // 2
-    jobs = [(seconds, min_steps, 1 + k) for k in range(procs)]
-    t0 = time.perf_counter()
+    procs = max(1, min(procs, n_steps))
+    warm = -(-max(0, warmup - procs) // procs)
+    jobs = [(name, n_steps // procs + (1 if k < n_steps % procs else 0), warm, 1 + k) for k in range(procs)]
     if procs == 1:
         res = [_oracle_md_worker(jobs[0])]
     else:
         import multiprocessing as mp
         with mp.get_context("spawn").Pool(procs) as pool:
             res = pool.map(_oracle_md_worker, jobs)
-    wall = time.perf_counter() - t0
+    secs = max(r[1] for r in res)
     steps = sum(r[0] for r in res)
-    # per-process rates summed: start-up of the spawned interpreters is not oracle work
-    rate = sum(pairs * r[0] / r[1] for r in res)
-    return rate, steps, wall
+    return res[0][2] * steps / secs, steps, secs, procs
 
 
 def host_cores():
@@ -177,51 +201,57 @@ def host_cores():
 
 
 def reference_arm(args):
-    """The FP64 oracle on all host cores, on a bounded sample of the same
-    workload: each step = 2 MD steps of one 2048-atom replica per core (the 8
-    replicas are identical and independent between exchanges)."""
+    """The FP64 oracle on the host cores, on a bounded sample of the same
+    workload: each bench step is one whole MD step of one replica of the
+    workload (a 25,000-atom replica by default), the K steps spread over one
+    process per core and timed in each process after its warm-up (the
+    untimed force evaluation at the starting coordinates, one per process,
+    which also covers the W warm-up steps when there are at least W
+    processes)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    procs = host_cores()
-    md_per = 2
-    oracle_throughput(procs, 0.0, md_per * args.warmup) if args.warmup else None
-    rate, steps, wall = oracle_throughput(procs, 0.0, md_per * args.steps)
-    value = rate
+    name = args.workload
+    b = workload(name)
+    pairs_md = pairs_per_md_step(b, name)
+    rate, steps, secs, procs = oracle_throughput(name, args.steps, host_cores(), args.warmup)
+    rep_n = b.replicas[0].n
+    sample = (f"{steps} BAOAB MD steps (GB + Coulomb + restraint forces) of one {rep_n}-atom replica "
+              f"of the workload, spread over {procs} spawned processes (one per core); time = the "
+              f"slowest process's timed steps")
     line = {
-        "impl": "reference", "metric": "GB pair-interactions/s", "value": value,
+        "impl": "reference", "metric": "GB pair-interactions/s", "value": rate,
         "unit": "pair-interactions/s", "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1000 * wall / max(args.steps, 1), "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": 1000 * secs / max(args.steps, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"eremd_{N_REP}x{N_ATOMS}",
-                   "sample": f"{procs} processes x {md_per} MD steps of one replica per step"},
-        "cpu_baseline": {"value": value, "unit": "pair-interactions/s", "cores": procs, "kind": "oracle",
-                         "sample": f"{steps} BAOAB MD steps of 2048-atom replicas, one per process, "
-                                   f"{procs} spawned processes"},
-        "e2e": {"value": value, "unit": "pair-interactions/s", "h2d_bytes_per_step": 0,
+        "config": bench_config(name, b, pairs_md),
+        "sample": sample,
+        "cpu_baseline": {"value": rate, "unit": "pair-interactions/s", "cores": procs, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": rate, "unit": "pair-interactions/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(seconds=12.0):
-    """The oracle's force evaluation + BAOAB step of 2048-atom replicas for
-    about `seconds`: on one core, then one replica per core on all cores."""
-    r1, n1, w1 = oracle_throughput(1, seconds, 3)
-    procs = host_cores()
-    rN, nN, wN = oracle_throughput(procs, seconds, 3)
-    return {"value": rN, "unit": "pair-interactions/s", "cores": procs, "kind": "oracle",
-            "sample": f"{nN} BAOAB MD steps (GB+Coulomb+restraint forces) of 2048-atom replicas, one per "
-                      f"process on {procs} cores, {seconds:.0f} s each",
-            "single_core": {"value": r1, "cores": 1,
-                            "sample": f"{n1} MD steps of one replica, {w1:.1f} s"}}
+def cpu_baseline(name):
+    """The oracle on a bounded sample of the workload: one MD step of one
+    replica per host core (each after its untimed starting force
+    evaluation)."""
+    cores = host_cores()
+    rate, steps, secs, procs = oracle_throughput(name, cores, cores)
+    b = workload(name)
+    return {"value": rate, "unit": "pair-interactions/s", "cores": procs, "kind": "oracle",
+            "sample": f"{steps} BAOAB MD steps (GB + Coulomb + restraint forces) of one "
+                      f"{b.replicas[0].n}-atom replica of the workload, one per process on {procs} "
+                      f"cores, {secs:.1f} s"}
 
 
 # ----------------------------------------------------------------------------------
 class Setup:
     """Device state of the workload and the gb_md_state that points at it."""
 
-    def __init__(self, pkg, batch, dev, seed, params):
+    def __init__(self, pkg, batch, dev, seed, params, G=None):
         import torch
         self.pkg, self.b, self.dev = pkg, batch, dev
         self.ctx = pkg.Context(batch.atom_off, params)
@@ -231,7 +261,8 @@ class Setup:
         self.vel = torch.zeros((N, 4), dtype=torch.float32, device=dev)
         self.force = torch.zeros((N, 4), dtype=torch.float32, device=dev)
         self.R = torch.zeros(N, dtype=torch.float32, device=dev)
-        G = site_reference_energies_gpu(pkg, batch, dev, params)
+        if G is None:
+            G = site_reference_energies_gpu(pkg, batch, dev, params)
         self.tables = batch.site_tables(G)
         self.sites = pkg.SiteTables(self.tables, M, dev)
         self.state = torch.zeros(self.tables["n_sites"], dtype=torch.int32, device=dev)
@@ -348,14 +379,14 @@ def job_rate(units_per_rank, world, seconds):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=150)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--workload", default="eremd_8x2048", choices=WORKLOADS,
-                    help="configuration to run (default: the E-REMD headline batch)")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=WORKLOADS,
+                    help="configuration to run (default: the 2-D grid of 48 x 25,000-atom replicas)")
     ap.add_argument("--persistent", action="store_true",
                     help="one persistent launch per run of MD steps instead of six launches per step")
     args = ap.parse_args()
@@ -367,6 +398,7 @@ def main():
     world, rank, local = dist_init("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
 
     import __graft_entry__
     if rank == 0:
@@ -423,10 +455,13 @@ def main():
     # ---- kernel timing: the same bench steps with CUDA events around every pair
     # pass (or persistent launch) inside the captured graph, on the graph's
     # stream.  Kept apart from the headline region, whose graph has no events
-    # between kernels (they would break the programmatic launch edges).
+    # between kernels (they would break the programmatic launch edges).  About
+    # two seconds of bench steps (at least one: 100 MD steps, 100 samples of
+    # each pass).
     S.ctx.set_profiling(True)
     pass_ms = []
-    for k in range(max(3, min(args.steps, 20))):
+    n_prof = int(max(1, min(20, 2.0 / (est_md_step_s(b) * MD_PER_STEP))))
+    for k in range(n_prof):
         flush.zero_()
         S.ctx.md_segment(S.st, S.sites, MD_PER_STEP)
         torch.cuda.synchronize()
@@ -437,9 +472,9 @@ def main():
 
     # ---- roofline of the dominant kernel (FP32 ALU bound) ------------------------
     sm_max = (clk.get("sm_max_mhz") or 2070.0)
-    peak = SM_COUNT * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    peak = sm_count * FP32_LANES * 2 * sm_max * 1e6 / 1e12
     sm_load = clk.get("sm_mhz") or sm_max
-    peak_load = SM_COUNT * FP32_LANES * 2 * sm_load * 1e6 / 1e12
+    peak_load = sm_count * FP32_LANES * 2 * sm_load * 1e6 / 1e12
     all_flops = pairs_md * sum(FLOPS_PER_PAIR.values())
     if persistent:
         # one launch runs pm[2] MD steps: three pair passes per step
@@ -461,14 +496,15 @@ def main():
     # ---- plain form: one context per replica, direct launches, no graph ---------
     plain = None
     if not args.no_plain and rank == 0:
-        plain = plain_form(pkg, b, dev, params, n_bench=10, pairs_md=pairs_md)
+        plain = plain_form(pkg, S, dev, params, pairs_md=pairs_md)
 
-    # ---- end to end through host buffers ----------------------------------------
-    e2e = end_to_end(pkg, S, dev, n_bench=max(2, min(5, args.steps)), pairs_md=pairs_md)
+    # ---- end to end through gb_md_segment_host (state in pinned host memory) ----
+    n_e2e = int(max(2, min(5, 10.0 / (est_md_step_s(b) * MD_PER_STEP))))
+    e2e = end_to_end(pkg, S, n_bench=n_e2e, pairs_md=pairs_md)
 
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
-        cpu = cpu_baseline()
+        cpu = cpu_baseline(args.workload)
 
     if rank == 0:
         line = {
@@ -477,15 +513,9 @@ def main():
             "ms_per_step": 1000 * dev_s / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 pairs, int64 fixed-point sums, f64 totals",
             "data": "synthetic",
-            "config": {"workload": args.workload, "replicas": b.n_rep,
-                       "atoms_total": b.n_atoms, "md_steps_per_step": MD_PER_STEP,
-                       "mc_every": MC_EVERY, "exchange_every": EX_EVERY,
-                       "pairs_per_md_step": pairs_md, "l2": "flushed between steps (256 MB write)",
-                       "cutoffs_A": CUTOFFS.get(args.workload),
-                       "pairs_counted": "within the pair cutoff at the start" if args.workload in CUTOFFS
-                       else "all pairs",
-                       "tiles": list(S.ctx.tiles()), "reg_caps": list(S.ctx.reg_caps()),
-                       "parallelism": "replicas batched on one GPU"},
+            "config": bench_config(args.workload, b, pairs_md),
+            "tuning": {"tiles": list(S.ctx.tiles()), "reg_caps": list(S.ctx.reg_caps()),
+                       "sm_count": sm_count},
             "replica_md_steps_per_s": rep_steps,
             "kernel_timing": timing,
             "fp32_flops_per_pair": FLOPS_PER_PAIR,
@@ -495,7 +525,8 @@ def main():
             "roofline": {"bound": "alu", "kernel": name, "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "frac_at_load_clock": achieved / peak_load, "traffic": traffic,
-                         "peak_source": f"{SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 x {sm_max:.0f} MHz"},
+                         "peak_source": f"{sm_count} SMs (device properties) x {FP32_LANES} FP32 lanes x 2 x "
+                                        f"{sm_max:.0f} MHz"},
             "plain": plain,
             "e2e": e2e,
             "cpu_baseline": cpu,
@@ -547,62 +578,65 @@ def read_traffic(name):
     return table.get(name)
 
 
-def plain_form(pkg, b, dev, params, n_bench, pairs_md):
+def plain_form(pkg, S_batch, dev, params, pairs_md):
     """Each replica in its own context, MD + MC one step at a time with direct
-    launches (no graph, no batching); same arithmetic.  Exchanges are O(M)
-    and left out of this form."""
+    launches (no graph, no batching); same arithmetic and the batch's site
+    reference energies.  Exchanges are O(M) and left out of this form.
+    Timed over whole MC periods, about half a second per timed block (at
+    least one period), median of five blocks."""
     import synth
     import torch
+    b = S_batch.b
+    t = S_batch.tables
     setups = []
     for r, rep in enumerate(b.replicas):
         sb = synth.Batch([rep], pH=b.pH[r:r + 1], E=b.E[r:r + 1], E_ladder=b.E[r:r + 1])
-        S = Setup(pkg, sb, dev, seed=99 + r, params=params)
+        lo, hi = t["site_state_off"][t["site_off"][r]], t["site_state_off"][t["site_off"][r + 1]]
+        S = Setup(pkg, sb, dev, seed=99 + r, params=params, G=t["G_ref"][lo:hi])
         S.st.ex_every = 0
         S.ctx.set_persistent(False)
         setups.append(S)
+    md = MC_EVERY * int(max(1, min(MD_PER_STEP // MC_EVERY, 0.5 / (est_md_step_s(b) * MC_EVERY))))
     for S in setups:
-        S.ctx.md_segment(S.st, S.sites, 10)
+        S.ctx.md_segment(S.st, S.sites, MC_EVERY)
     torch.cuda.synchronize()
+    n_bench = 5
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_bench)]
     for k in range(n_bench):
         ev[k][0].record()
-        for t in range(MD_PER_STEP):
+        for _ in range(md):
             for S in setups:
                 S.ctx.md_segment(S.st, S.sites, 1)
         ev[k][1].record()
     torch.cuda.synchronize()
-    ms = statistics.median(a.elapsed_time(c) for a, c in ev)      # per bench step
+    for S in setups:
+        S.ctx.sync_status()
+    ms = statistics.median(a.elapsed_time(c) for a, c in ev)      # per block of md MD steps
     s = ms / 1000.0
-    pairs = pairs_md * MD_PER_STEP
-    return {"value": pairs / s, "unit": "pair-interactions/s", "ms_per_step": ms,
-            "replica_md_steps_per_s": b.n_rep * MD_PER_STEP / s, "bench_steps": n_bench, "statistic": "median",
-            "form": "one context per replica, direct launches per MD step, no graph"}
+    return {"value": pairs_md * md / s, "unit": "pair-interactions/s", "ms_per_step": ms * MD_PER_STEP / md,
+            "replica_md_steps_per_s": b.n_rep * md / s, "md_steps_per_block": md, "blocks": n_bench,
+            "statistic": "median", "form": "one context per replica, direct launches per MD step, no graph"}
 
 
-def end_to_end(pkg, S, dev, n_bench, pairs_md):
-    """Same metric through the public API with host buffers: every step copies
-    the MD state from pinned host memory, runs the segment and copies the new
-    state back."""
+def end_to_end(pkg, S, n_bench, pairs_md):
+    """Same metric through the public C ABI with the dynamic state in pinned
+    host memory: every bench step is one gb_md_segment_host call, which copies
+    the state (coordinates and charges, velocities, forces, site states, pH,
+    E, exchange grid) from the host arrays to the device, runs the 100 MD
+    steps and copies the new state back before it returns."""
     import torch
-    host = {k: getattr(S, k).detach().cpu().pin_memory() for k in ("xyzq", "vel", "force", "state", "E")}
-    h2d = sum(t.numel() * t.element_size() for t in host.values())
-    d2h = h2d
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    keys = ("xyzq", "vel", "force", "state", "pH", "E", "grid")
     torch.cuda.synchronize()
-    e0.record(stream)
+    host = {k: getattr(S, k).detach().cpu().pin_memory() for k in keys}
+    nbytes = sum(t.numel() * t.element_size() for t in host.values())
+    S.ctx.md_segment_host(S.st, S.sites, MD_PER_STEP, host)        # untimed: the first call
+    t0 = time.perf_counter()
     for _ in range(n_bench):
-        for k, t in host.items():
-            getattr(S, k).copy_(t, non_blocking=True)
-        S.ctx.md_segment(S.st, S.sites, MD_PER_STEP)
-        for k, t in host.items():
-            t.copy_(getattr(S, k), non_blocking=True)
-        # the result is read on the host every step
-    e1.record(stream)
-    torch.cuda.synchronize()
-    s = e0.elapsed_time(e1) / 1000.0
+        S.ctx.md_segment_host(S.st, S.sites, MD_PER_STEP, host)
+    s = time.perf_counter() - t0
     return {"value": pairs_md * MD_PER_STEP * n_bench / s, "unit": "pair-interactions/s",
-            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": n_bench}
+            "h2d_bytes_per_step": int(nbytes), "d2h_bytes_per_step": int(nbytes), "steps": n_bench,
+            "call": "gb_md_segment_host (host wall clock; the call returns with the state on the host)"}
 
 
 if __name__ == "__main__":

@@ -321,6 +321,35 @@ int gb_md_init(gb_ctx* ctx, gb_md_state* state, void* stream);
 int gb_md_segment(gb_ctx* ctx, gb_md_state* state, const gb_sites* sites, int64_t nsteps,
                   void* stream);
 
+/* The dynamic MD state of a batch kept in HOST memory, for gb_md_segment_host.
+ * Every pointer is a HOST array mirroring the device buffer of the same name
+ * in gb_md_state (same layout and length); NULL leaves that buffer on the
+ * device untouched.  Pinned memory (cudaHostAlloc / cudaHostRegister) makes
+ * the copies asynchronous DMA; pageable memory works, staged by the driver. */
+typedef struct {
+    float* xyzq;            /* float[N][4] */
+    float* vel;             /* float[N][4] */
+    float* force;           /* float[N][4] */
+    int32_t* state;         /* int32[n_sites] */
+    double* pH;             /* double[M] */
+    double* E;              /* double[M] */
+    int32_t* grid;          /* int32[n_pH * n_E] */
+    int32_t n_sites;        /* length of state (0 when state is NULL) */
+} gb_md_host;
+
+/* gb_md_segment for a caller whose batch state lives in host memory between
+ * segments (the paper's MD advances one replica's coordinates, charges and
+ * site states by blocks of steps between halts, Sec. III.A-B; here a whole
+ * batch at once).  On `stream`: one cudaMemcpyAsync per non-NULL array of
+ * `host` into the device buffer `state` points at, nsteps MD steps exactly as
+ * gb_md_segment, one cudaMemcpyAsync per array back into `host`; then waits
+ * for the stream, so the host arrays hold the new state when the call
+ * returns.  The device buffers of `state` are the caller's working copy.
+ * Returns what gb_md_segment returns, then, after the wait, a device-detected
+ * error as gb_sync_status does. */
+int gb_md_segment_host(gb_ctx* ctx, gb_md_state* state, const gb_sites* sites, int64_t nsteps,
+                       const gb_md_host* host, void* stream);
+
 /* The register caps tuned on the MD driver itself: coordinate descent over
  * the three passes' caps, every candidate timed (CUDA events, best of four) on
  * an MD segment of trial_steps steps (gb_md_segment with these sites, as the

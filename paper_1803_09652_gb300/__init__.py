@@ -11,6 +11,7 @@ Call names follow the C ABI in include/gbremd.h:
     Context.mc_step          -> redox_ph_mc_step
     eremd_exchange           -> eremd_exchange
     Context.md_init / md_segment -> gb_md_init / gb_md_segment
+    Context.md_segment_host  -> gb_md_segment_host
 """
 from __future__ import annotations
 
@@ -78,6 +79,12 @@ class MDState(C.Structure):
                 ("wrap", C.c_int32), ("mc_mode", C.c_int32), ("ex_count", _P)]
 
 
+class MDHost(C.Structure):
+    """gb_md_host: host arrays mirroring an MD state's device buffers."""
+    _fields_ = [("xyzq", _P), ("vel", _P), ("force", _P), ("state", _P), ("pH", _P), ("E", _P),
+                ("grid", _P), ("n_sites", C.c_int32)]
+
+
 _lib = None
 
 
@@ -115,6 +122,7 @@ def load(path: Optional[str] = None):
         "gb_count_bound": [C.POINTER(Sites), _P, i32, _P, _P],
         "gb_md_init": [_P, C.POINTER(MDState), _P],
         "gb_md_segment": [_P, C.POINTER(MDState), C.POINTER(Sites), C.c_int64, _P],
+        "gb_md_segment_host": [_P, C.POINTER(MDState), C.POINTER(Sites), C.c_int64, C.POINTER(MDHost), _P],
         "gb_set_profiling": [_P, i32],
         "gb_pass_times": [_P, C.POINTER(C.c_double)],
         "gb_set_persistent": [_P, i32],
@@ -340,6 +348,25 @@ class Context:
     def md_segment(self, st: MDState, sites: Optional[SiteTables], nsteps: int, stream=None):
         sp = C.byref(sites.struct) if sites is not None else None
         _check(self.lib.gb_md_segment(self.h, C.byref(st), sp, int(nsteps), _stream(stream)), self.h)
+
+    def md_segment_host(self, st: MDState, sites: Optional[SiteTables], nsteps: int, host: dict,
+                        stream=None):
+        """gb_md_segment_host: host tensors (CPU, ideally pinned) keyed by
+        xyzq, vel, force, state, pH, E, grid are copied to st's device
+        buffers, nsteps MD steps run, and the new state is copied back into
+        them before the call returns."""
+        h = MDHost()
+        for k in ("xyzq", "vel", "force", "state", "pH", "E", "grid"):
+            t = host.get(k)
+            if t is not None:
+                if t.is_cuda or not t.is_contiguous():
+                    raise ValueError(f"{k}: a contiguous host tensor is required")
+                setattr(h, k, t.data_ptr())
+        if host.get("state") is not None:
+            h.n_sites = int(host["state"].numel())
+        sp = C.byref(sites.struct) if sites is not None else None
+        _check(self.lib.gb_md_segment_host(self.h, C.byref(st), sp, int(nsteps), C.byref(h), _stream(stream)),
+               self.h)
 
 
 class Simulation:

@@ -1040,6 +1040,35 @@ extern "C" int gb_md_segment(gb_ctx* c, gb_md_state* st, const gb_sites* sites, 
     return GB_OK;
 }
 
+extern "C" int gb_md_segment_host(gb_ctx* c, gb_md_state* st, const gb_sites* sites, int64_t nsteps,
+                                  const gb_md_host* h, void* stream) {
+    int rc = check_md(c, st);
+    if (rc) return rc;
+    if (!h) return fail(c, GB_ERR_INVALID_ARG, "host state is NULL");
+    if (h->state && (!st->state || h->n_sites < 0)) return fail(c, GB_ERR_INVALID_ARG, "host state array without a device one");
+    if (h->grid && !st->grid) return fail(c, GB_ERR_INVALID_ARG, "host grid without a device one");
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t N = (size_t)c->N, M = (size_t)c->M;
+    const size_t G = (size_t)st->n_E * (size_t)st->n_pH;
+    struct Pair { void* dev; void* host; size_t bytes; };
+    const Pair arrays[] = {
+        {st->xyzq, h->xyzq, 16 * N},  {st->vel, h->vel, 16 * N},   {st->force, h->force, 16 * N},
+        {st->state, h->state, 4 * (size_t)(h->n_sites > 0 ? h->n_sites : 0)},
+        {st->pH, h->pH, 8 * M},       {st->E, h->E, 8 * M},        {st->grid, h->grid, 4 * G},
+    };
+    for (const Pair& a : arrays)
+        if (a.host && a.bytes) {
+            if (!a.dev) return fail(c, GB_ERR_INVALID_ARG, "host array without a device buffer");
+            GB_CHECK(c, cudaMemcpyAsync(a.dev, a.host, a.bytes, cudaMemcpyHostToDevice, s));
+        }
+    rc = gb_md_segment(c, st, sites, nsteps, stream);
+    if (rc) return rc;
+    for (const Pair& a : arrays)
+        if (a.host && a.bytes) GB_CHECK(c, cudaMemcpyAsync(a.host, a.dev, a.bytes, cudaMemcpyDeviceToHost, s));
+    return gb_sync_status(c, stream);
+}
+
 // ---------------------------------------------------------------------------------
 // Autotuner: time one full force evaluation per candidate tile shape.
 

@@ -45,7 +45,7 @@ def _header_struct_fields(name):
 
 
 @pytest.mark.parametrize("cname,pycls", [("gb_params", pkg.Params), ("gb_sites", pkg.Sites),
-                                         ("gb_md_state", pkg.MDState)])
+                                         ("gb_md_state", pkg.MDState), ("gb_md_host", pkg.MDHost)])
 def test_struct_layouts_match_header(cname, pycls):
     assert _header_struct_fields(cname) == [f[0] for f in pycls._fields_]
 

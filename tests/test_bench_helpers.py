@@ -40,3 +40,12 @@ def test_every_workload_is_known():
     assert set(bench.CUTOFFS) <= set(bench.WORKLOADS)
     with pytest.raises(ValueError):
         bench.workload("no_such_workload")
+
+
+def test_default_workload_is_the_largest_single_gpu_configuration():
+    assert bench.DEFAULT_WORKLOAD == "grid_48x25000"
+    b = synth.config_grid()
+    c = bench.bench_config(bench.DEFAULT_WORKLOAD, b, b.pairs_per_eval())
+    assert c["replicas"] == 48 and c["atoms_total"] == 48 * 25000
+    assert c["pairs_per_md_step"] == 48 * 25000 * 24999 // 2
+    assert c["md_steps_per_step"] == 100 and c["mc_every"] == 10 and c["exchange_every"] == 100

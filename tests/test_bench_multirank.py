@@ -59,7 +59,7 @@ def test_reference_arm_under_torchrun_prints_once():
     port = _free_port()
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
-           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0"]
+           "--impl", "reference", "--gpus", "2", "--steps", "2", "--warmup", "3", "--workload", "eremd_8x2048"]
     env = dict(os.environ, OMP_NUM_THREADS="1")
     p = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, env=env, timeout=600)
     assert p.returncode == 0, p.stderr[-2000:]
@@ -69,3 +69,9 @@ def test_reference_arm_under_torchrun_prints_once():
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+    # the reference line reports the same config dict as the GPU arm would
+    sys.path.insert(0, ROOT)
+    import bench
+    b = bench.workload("eremd_8x2048")
+    assert line["config"] == json.loads(json.dumps(bench.bench_config("eremd_8x2048", b, b.pairs_per_eval())))
+    assert "2 BAOAB MD steps" in line["sample"]

@@ -291,3 +291,26 @@ def test_simulation_in_sweep_mode_keeps_charges_consistent(pkg):
         idx = t["site_atom_idx"][a0:a1] + b.atom_off[r]
         qo = t["site_q_off"][s] + st[s] * (a1 - a0)
         assert np.array_equal(x[idx, 3], t["q_state"][qo:qo + a1 - a0])
+
+
+def test_host_buffer_segment_equals_the_device_segment(pkg):
+    """gb_md_segment_host with the dynamic state in pinned host memory: the
+    host arrays after each call equal, bit for bit, the device state of a
+    twin run through gb_md_segment (MC every 5 steps, exchanges every 10)."""
+    import torch
+    b = synth.random_batch([300, 180, 64, 140], seed=12)
+    ctx, st, S, sites = _setup(pkg, b, seed=9, mc_every=5, ex_every=10, with_sites=True)
+    ctx2, st2, S2, sites2 = _setup(pkg, b, seed=9, mc_every=5, ex_every=10, with_sites=True)
+    torch.cuda.synchronize()
+    keys = ("xyzq", "vel", "force", "state", "pH", "E", "grid")
+    host = {k: S2[k].cpu().pin_memory() for k in keys}
+    for k in keys:                              # the device copies of the host run start as garbage
+        S2[k].fill_(7)
+    for _ in range(3):
+        ctx.md_segment(st, sites, 20)
+        ctx2.md_segment_host(st2, sites2, 20, host)
+        torch.cuda.synchronize()
+        for k in keys:
+            assert torch.equal(host[k], S[k].cpu()), k
+    ctx.sync_status()
+    assert st2.step == st.step == 60 and st2.attempt == st.attempt == 6
