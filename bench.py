@@ -387,6 +387,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=WORKLOADS,
                     help="configuration to run (default: the 2-D grid of 48 x 25,000-atom replicas)")
+    ap.add_argument("--max-replicas", type=int, default=0,
+                    help="keep only the first M replicas of the workload (small cases for profiler captures)")
     ap.add_argument("--persistent", action="store_true",
                     help="one persistent launch per run of MD steps instead of six launches per step")
     args = ap.parse_args()
@@ -410,6 +412,10 @@ def main():
 
     params = pkg.default_params(rep_k=100.0, rep_sigma=2.5, **CUTOFFS.get(args.workload, {}))
     b = workload(args.workload)
+    if 0 < args.max_replicas < b.n_rep:
+        import synth
+        M = args.max_replicas
+        b = synth.Batch(b.replicas[:M], pH=b.pH[:M], E=b.E[:M], name=b.name)
     S = Setup(pkg, b, dev, seed=1234 + rank, params=params)
     if not args.no_autotune:
         S.ctx.autotune(S.xyzq, S.rad)

@@ -278,7 +278,8 @@ int gb_count_bound(const gb_sites* sites, const int32_t* state, int32_t kind,
  * redox, Sec. III.A) and neighbour exchanges every ex_every steps (Sec.
  * III.B) along the E ladder (ex_dim 0) or pH ladder (ex_dim 1), alternating
  * between E and pH lines when ex_dim is 2 (two-dimensional grid).  Noise:
- * Philox4x64-10, key (seed, 0), counter (replica, step, 4, atom), Box-Muller.
+ * Philox4x64-10, key (seed, 0), counter (rep_base + replica, step, 4, atom),
+ * Box-Muller; the Monte Carlo attempts count replicas from rep_base too.
  * The state buffers are owned by the caller and updated in place. */
 typedef struct {
     float* xyzq;            /* float[N][4] positions + current charges */
@@ -309,6 +310,12 @@ typedef struct {
                                the wrap pair has its first slot at the ladder's end).  An
                                exchange skipped for a corrupt state counts as neither.
                                The caller zeroes it; gb_autotune_md leaves it as it was. */
+    int64_t rep_base;       /* global index of this batch's replica 0 in the Philox counters
+                               of the MD noise and the Monte Carlo attempts (>= 0; 0 when the
+                               batch is the whole ensemble).  A replica ensemble split over
+                               processes gives each part the index of its first replica, so
+                               that every replica draws the numbers it would draw in one
+                               batch. */
 } gb_md_state;
 
 /* Advance the batch by nsteps MD steps.  Step t (1-based, absolute) is

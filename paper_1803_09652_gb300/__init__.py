@@ -12,6 +12,7 @@ Call names follow the C ABI in include/gbremd.h:
     eremd_exchange           -> eremd_exchange
     Context.md_init / md_segment -> gb_md_init / gb_md_segment
     Context.md_segment_host  -> gb_md_segment_host
+Replica ensembles split over processes: shard.ShardedSimulation.
 """
 from __future__ import annotations
 
@@ -76,7 +77,7 @@ class MDState(C.Structure):
                 ("kT", C.c_double), ("bond_k", C.c_float), ("bond_r0", C.c_float),
                 ("seed", C.c_uint64), ("step", C.c_uint64), ("attempt", C.c_uint64),
                 ("mc_every", C.c_int32), ("ex_every", C.c_int32), ("ex_dim", C.c_int32),
-                ("wrap", C.c_int32), ("mc_mode", C.c_int32), ("ex_count", _P)]
+                ("wrap", C.c_int32), ("mc_mode", C.c_int32), ("ex_count", _P), ("rep_base", C.c_int64)]
 
 
 class MDHost(C.Structure):
@@ -382,12 +383,14 @@ class Simulation:
     row p and E column e; exchanges run when n_E * n_pH == M > 1, along E
     (ex_dim 0), pH (1) or alternating (2, the default on a 2-D grid).
     Attributes xyzq, vel, force, R, state, pH, E, grid and ex_count (the
-    exchange counters of gb_md_state) are the live device tensors."""
+    exchange counters of gb_md_state) are the live device tensors.  rep_base:
+    global index of replica 0 in the random-number counters (a part of an
+    ensemble split over processes; shard.ShardedSimulation sets it)."""
 
     def __init__(self, atom_off, xyzq, rad_screen, params: Optional[Params] = None, sites=None, pH=None,
                  E=None, E_ladder=None, pH_ladder=None, *, dt=0.002, friction=10.0, mass=12.0,
                  temperature=300.0, bond_k=300.0, bond_r0=1.5, seed=0, mc_every=10, ex_every=100,
-                 ex_dim=None, wrap=True, mc_mode=0, device=0):
+                 ex_dim=None, wrap=True, mc_mode=0, device=0, rep_base=0):
         import torch
         dev = torch.device("cuda", device)
         self.ctx = Context(atom_off, params, device)
@@ -426,6 +429,7 @@ class Simulation:
         st.ex_dim = (2 if n_pH > 1 else 0) if ex_dim is None else ex_dim
         st.wrap, st.mc_mode = 1 if wrap else 0, mc_mode
         st.ex_count = self.ex_count.data_ptr()
+        st.rep_base = int(rep_base)
         self.st = st
         self.ctx.md_init(st)
 

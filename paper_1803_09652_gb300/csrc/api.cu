@@ -744,6 +744,7 @@ gbk::MDArgs md_args(const gb_ctx* c, const gb_md_state* st) {
     m.bond_k = st->bond_k;
     m.bond_r0 = st->bond_r0;
     m.seed = st->seed;
+    m.rep_base = (u64)st->rep_base;
     return m;
 }
 
@@ -756,6 +757,7 @@ int check_md(gb_ctx* c, const gb_md_state* st) {
     if (!(st->dt >= 0) || !(st->mass > 0) || !(st->kT > 0) || !(st->friction >= 0))
         return fail(c, GB_ERR_INVALID_ARG, "invalid MD constants");
     if (st->mc_mode != 0 && st->mc_mode != 1) return fail(c, GB_ERR_INVALID_ARG, "mc_mode must be 0 or 1");
+    if (st->rep_base < 0) return fail(c, GB_ERR_INVALID_ARG, "rep_base < 0");
     return GB_OK;
 }
 
@@ -791,6 +793,7 @@ int enqueue_mc(gb_ctx* c, gb_md_state* st, const gb_sites* sites, int64_t k, cud
         a.cut2 = c->p.cut * c->p.cut;
         a.seed = st->seed;
         a.step = (u64)k;
+        a.rep_base = (u64)st->rep_base;
         a.ctr = c->ctr;
         a.kind = kind;
         a.state = st->state;

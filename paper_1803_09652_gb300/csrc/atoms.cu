@@ -133,7 +133,7 @@ __global__ void k_md_step(AtomArgs A, MDArgs m, float4* boxes, const int* tile_o
         if (mode & MD_OPEN) {
             const u64 step = m.ctr[0] + (u64)step_in_block + 1;
             x = m.xyzq[g];
-            baoab_first(m, x, v, f, md_normals(m.seed, (u64)r, step, (u64)i));
+            baoab_first(m, x, v, f, md_normals(m.seed, m.rep_base + (u64)r, step, (u64)i));
             m.xyzq[g] = x;
         }
         m.vel[g] = v;
@@ -186,7 +186,7 @@ struct MCPick {
 // Site and state proposal of replica r (Sec. III.A, III.A.1).
 __device__ __forceinline__ MCPick mc_pick(const MCArgs& A, int r) {
     const u64 step = (A.ctr ? A.ctr[0] : 0) + A.step;
-    const Philox4 w = philox4x64((u64)r, step, 1 + (u64)A.kind, 0, A.seed, 0);
+    const Philox4 w = philox4x64(A.rep_base + (u64)r, step, 1 + (u64)A.kind, 0, A.seed, 0);
     MCPick pk;
     pk.site = -1;
     pk.cur = pk.nxt = 0;
@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(256) k_sweep_decide(MCArgs A) {
     int cur = 0;
     for (int i = 0; i < L.n_sites; ++i) {
         if (tid == 0) {
-            const Philox4 w = philox4x64((u64)r, step, 5 + (u64)A.kind, (u64)i, A.seed, 0);
+            const Philox4 w = philox4x64(A.rep_base + (u64)r, step, 5 + (u64)A.kind, (u64)i, A.seed, 0);
             const int j = i + pick_int(w.w[0], L.n_sites - i);
             const int t = s_order[i];
             s_order[i] = s_order[j];

@@ -134,6 +134,7 @@ struct MDArgs {
     float c1, c2;              // exp(-gamma dt), sqrt((1 - c1^2) kT ACCEL / m)
     float bond_k, bond_r0;
     u64 seed;
+    u64 rep_base;              // global index of replica 0 in the Philox counters
 };
 
 // MD half steps between force evaluations (k_md_step): MD_CLOSE stores the
@@ -175,6 +176,7 @@ struct MCArgs {
     float cut2;                // pair cutoff squared (0: none)
     u64 seed;
     u64 step;
+    u64 rep_base;              // global index of replica 0 in the Philox counters
     const u64* ctr;            // when non-null the step is ctr[0] + step
     int32_t kind;
     int32_t* state;

@@ -89,7 +89,7 @@ __device__ __forceinline__ void tile_halfsteps(const PersistArgs& P, int r, int 
         }
         if (first) {
             float4 x = __ldcg(&m.xyzq[g]);
-            baoab_first(m, x, v, f, md_normals(m.seed, (u64)r, step, (u64)i));
+            baoab_first(m, x, v, f, md_normals(m.seed, m.rep_base + (u64)r, step, (u64)i));
             m.xyzq[g] = x;
         } else {
             m.force[g] = f;
