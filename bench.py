@@ -193,6 +193,12 @@ def oracle_throughput(name, n_steps, procs, warmup=0):
     return res[0][2] * steps / secs, steps, secs, procs
 
 
+def synth_one(b):
+    """The batch of replica 0 alone."""
+    import synth
+    return synth.Batch([b.replicas[0]], pH=b.pH[:1], E=b.E[:1])
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -240,15 +246,18 @@ def reference_arm(args):
 
 
 def cpu_baseline(name):
-    """The oracle on a bounded sample of the workload: one MD step of one
-    replica per host core (each after its untimed starting force
-    evaluation)."""
+    """The oracle on a bounded sample of the workload: MD steps of one
+    replica in one process per host core (each after its untimed starting
+    force evaluation), about ten seconds of them per process (at least one
+    step; the oracle does about 6.5e6 pair interactions per second on a
+    core)."""
     cores = host_cores()
-    rate, steps, secs, procs = oracle_throughput(name, cores, cores)
     b = workload(name)
+    per = max(1, int(round(10.0 * 6.5e6 / max(pairs_per_md_step(synth_one(b), name), 1))))
+    rate, steps, secs, procs = oracle_throughput(name, cores * per, cores)
     return {"value": rate, "unit": "pair-interactions/s", "cores": procs, "kind": "oracle",
             "sample": f"{steps} BAOAB MD steps (GB + Coulomb + restraint forces) of one "
-                      f"{b.replicas[0].n}-atom replica of the workload, one per process on {procs} "
+                      f"{b.replicas[0].n}-atom replica of the workload, {per} per process on {procs} "
                       f"cores, {secs:.1f} s"}
 
 
@@ -502,7 +511,7 @@ def main():
                   "pass_tflops": {k: pairs_md * FLOPS_PER_PAIR[k] / (float(v) * 1e-3) / 1e12
                                   for k, v in zip(PASS_NAMES, pm)}}
     step_fp32 = all_flops * MD_PER_STEP * args.steps / dev_s / 1e12
-    traffic = read_traffic(name)
+    traffic = read_traffic(name, b.n_atoms) if args.workload == DEFAULT_WORKLOAD else None
 
     # ---- plain form: one context per replica, direct launches, no graph ---------
     plain = None
@@ -566,13 +575,14 @@ def pair_source_hash():
     return h.hexdigest()[:16]
 
 
-def read_traffic(name):
-    """DRAM bytes per launch of `name` from the committed ncu summary; None when
-    there is none or the pair-kernel sources changed since it was captured."""
+def read_traffic(name, atoms_total):
+    """DRAM bytes per launch of `name` from the committed ncu summary, scaled
+    from the captured replica to the launch's atoms; None when there is none
+    or the pair-kernel sources changed since it was captured."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path):
         return None
-    table, src = {}, None
+    table, src, atoms = {}, None, None
     for line in open(path):
         parts = line.split()
         if len(parts) < 2 or parts[0].startswith("#"):
@@ -581,12 +591,15 @@ def read_traffic(name):
             src = parts[1]
             continue
         try:
-            table[parts[0]] = float(parts[1])
+            if parts[0] == "atoms":
+                atoms = int(parts[1])
+            else:
+                table[parts[0]] = float(parts[1])
         except ValueError:
             pass
-    if src != pair_source_hash():
+    if src != pair_source_hash() or name not in table or not atoms:
         return None
-    return table.get(name)
+    return table[name] * atoms_total / atoms
 
 
 def plain_form(pkg, S_batch, dev, params, pairs_md):
