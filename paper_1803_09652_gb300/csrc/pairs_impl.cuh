@@ -354,7 +354,8 @@ __device__ __forceinline__ void load_xas(const PairArgs& A, int64_t base, int n,
 // --- pass 1: Born integrals I_i = sum_j H(r_ij; a_i, s_j) -----------------------
 struct Born {
     static constexpr int NQ = 1;      // int64 i-side accumulators per atom (shared memory)
-    static constexpr int UNROLL = 2;  // rotation steps unrolled (measured best per pass)
+    static constexpr int UNROLL = 2;  // rotation steps unrolled (measured best per pass) ...
+    static constexpr int UNROLL_FAR = 4;   // ... and in far blocks
     static constexpr bool RADIUS_CUT = true;   // EF_CUT: the cutoff is rgbmax
     struct IState {
         f2 nx, ny, nz, a, s, s2, hs3;   // nx = -x
@@ -501,6 +502,7 @@ struct Born {
 struct Energy {
     static constexpr int NQ = 5;      // fx, fy, fz, dE/dR, dE/dq (shared memory)
     static constexpr int UNROLL = 2;
+    static constexpr int UNROLL_FAR = 2;
     static constexpr bool RADIUS_CUT = false;  // EF_CUT: the cutoff is `cut`
     struct IState {
         f2 nx, ny, nz, q, R, nh;
@@ -697,6 +699,7 @@ struct Energy {
 struct Chain {
     static constexpr int NQ = 3;      // fx, fy, fz (shared memory)
     static constexpr int UNROLL = 2;
+    static constexpr int UNROLL_FAR = 4;
     static constexpr bool RADIUS_CUT = true;   // EF_CUT: the cutoff is rgbmax
     struct IState {
         f2 nx, ny, nz, a, s, s2, hs3, c;
@@ -876,7 +879,7 @@ __device__ __forceinline__ void run_tile(const PairArgs& A, const typename P::IS
     constexpr int K0 = (MODE == M_DX) ? 1 : 0, K1 = (MODE == M_DX) ? 17 : 32;
     // straddling blocks carry the long restricted-integral code: not unrolled,
     // so that it fits the instruction cache
-    constexpr int U = (FLAGS & EF_STRADDLE) ? 1 : P::UNROLL;
+    constexpr int U = (FLAGS & EF_STRADDLE) ? 1 : (FAR ? P::UNROLL_FAR : P::UNROLL);
 #pragma unroll U
     for (int k = K0; k < K1; ++k) {
         // the next step's j data are fetched before this step's arithmetic, so
