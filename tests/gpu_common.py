@@ -110,3 +110,22 @@ def oracle_pool(n_jobs):
     import os
     n = max(2, min(n_jobs, (os.cpu_count() or 2) - 1))
     return mp.get_context("spawn").Pool(n)
+
+
+def oracle_mc_job(args):
+    """The oracle's Monte Carlo attempt of replica r alone (a module-level
+    function for spawned worker processes).  The oracle draws its random
+    numbers by replica index, so replica r runs behind r empty replicas.
+    args: (r, x, q, R (float64, the replica's), site table of the replica
+    alone (synth layout), states, pH, E, kT, seed, step, kind).  Returns
+    dict(dG, acc, thresh, site, new_state) of replica r."""
+    r, x, q, R, t, st, pH, E, kT, seed, step, kind = args
+    n = len(q)
+    off = np.array([0] * (r + 1) + [n], dtype=np.int64)
+    tt = dict(t)
+    tt["site_off"] = np.concatenate([np.zeros(r, np.int32), np.asarray(t["site_off"], np.int32)])
+    pHv = np.full(r + 1, float(pH))
+    Ev = np.full(r + 1, float(E))
+    o = oracle.mc_step(off, np.ascontiguousarray(x), np.ascontiguousarray(q).copy(), np.ascontiguousarray(R), tt,
+                       np.ascontiguousarray(st, np.int32).copy(), pHv, Ev, kT, seed, step, kind, oracle_params())
+    return {k: v[r] for k, v in o.items()}

@@ -9,6 +9,8 @@ benchmark uses (one context over the whole batch, default tiles).
 * uneven batch (64 replicas, 500..20000 atoms): every replica element by
   element, up to the largest (18134 atoms), plus properties that hold at any
   size.
+* Monte Carlo attempts (both kinds) on every uneven replica and on three
+  25,000-atom grid replicas against the oracle's two-evaluation energy change.
 * 48 x 25000 grid batch: one 25,000-atom replica element by element (energy,
   forces, Born radii, dE/dq), identical results on identical replicas, and the
   same properties.  At these sizes the FP32 far-field terms, the int64
@@ -23,8 +25,8 @@ import pytest
 
 import oracle
 import synth
-from gpu_common import (DG_ABS, E_REL, F_ABS, KT, PHI_ABS, R_REL, device, energy_rel_err,
-                        oracle_energy_forces_job, oracle_params, oracle_pool, to_dev)
+from gpu_common import (DG_ABS, E_REL, F_ABS, KT, PHI_ABS, R_REL, device, energy_rel_err, oracle_energy_forces_job,
+                        oracle_mc_job, oracle_params, oracle_pool, to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -232,3 +234,76 @@ def test_single_replica_50000_atoms(pkg):
     assert np.max(np.abs(out["R"][idx] - R) / R) <= R_REL
     assert np.all(np.isfinite(out["F"])) and np.all(out["R"] > 0)
     _properties(out, b)
+
+
+def _mc_full(pkg, b, reps, kinds=(0, 1), seed=3, step=10):
+    """GPU single-site attempts on the whole batch, one per kind, each from
+    the initial states (all 0, G_ref = 0), and the oracle's attempt for each
+    listed replica and kind (its two-evaluation energy change), one spawned
+    worker per replica and kind.  Returns {kind: (dG, acc, {r: oracle})}."""
+    import torch
+    from paper_1803_09652_gb300.shard import slice_sites
+    dev = device()
+    t = b.site_tables()                     # G_ref = 0: an input like any other
+    xyzq, rad = to_dev(b, dev)
+    ctx = pkg.Context(b.atom_off)
+    R = ctx.born_radii(xyzq, rad)
+    sites = pkg.SiteTables(t, b.n_rep, dev)
+    pH, E = torch.as_tensor(b.pH, device=dev), torch.as_tensor(b.E, device=dev)
+    gpu = {}
+    for kind in kinds:
+        state = torch.zeros(t["n_sites"], dtype=torch.int32, device=dev)
+        x4 = xyzq.clone()
+        dG, acc = ctx.mc_step(sites, x4, R, pH, E, KT, seed, step, kind, state)
+        torch.cuda.synchronize()
+        gpu[kind] = (dG.cpu().numpy(), acc.cpu().numpy())
+    ctx.sync_status()
+    Rn = R.double().cpu().numpy()
+    x, q, rho, scr, off = oracle.batch_arrays(b)
+    jobs, keys = [], []
+    for kind in kinds:
+        for r in reps:
+            a, c = off[r], off[r + 1]
+            tr = slice_sites(t, r, r + 1)
+            jobs.append((r, x[a:c], q[a:c], Rn[a:c], tr, np.zeros(tr["n_sites"], np.int32), b.pH[r], b.E[r], KT,
+                         seed, step, kind))
+            keys.append((kind, r))
+    # largest replicas first, so that the pool's tail is short
+    order = np.argsort([-(off[r + 1] - off[r]) for _, r in keys])
+    pool = oracle_pool(len(jobs))
+    try:
+        outs = pool.map(oracle_mc_job, [jobs[i] for i in order])
+    finally:
+        pool.terminate()
+        pool.join()
+    ctx.close()
+    res = {kind: (gpu[kind][0], gpu[kind][1], {}) for kind in kinds}
+    for i, o in zip(order, outs):
+        kind, r = keys[i]
+        res[kind][2][r] = o
+    return res
+
+
+def test_mc_energy_change_every_uneven_replica(pkg, uneven):
+    """Protonation (multi-state sites, 2-5 states) and redox attempts on every
+    replica of the uneven batch, 500 to 18,134 atoms, against the oracle's
+    two full energy evaluations at the same radii."""
+    b = uneven
+    for kind, (dG, acc, ref) in _mc_full(pkg, b, list(range(b.n_rep))).items():
+        n_near = 0
+        for r, o in ref.items():
+            assert abs(dG[r] - o["dG"]) <= DG_ABS, (kind, r, dG[r], o["dG"])
+            if acc[r] != o["acc"]:
+                assert abs(o["dG"] - o["thresh"]) <= DG_ABS, (kind, r)
+                n_near += 1
+        assert n_near <= 1
+
+
+def test_mc_energy_change_grid_replicas(pkg):
+    """Redox and protonation attempts on three 25,000-atom replicas of the
+    2-D grid (each at its own pH and E) against the oracle."""
+    b = synth.config_grid()
+    for kind, (dG, acc, ref) in _mc_full(pkg, b, [0, 17, 47]).items():
+        for r, o in ref.items():
+            assert abs(dG[r] - o["dG"]) <= DG_ABS, (kind, r, dG[r], o["dG"])
+            assert acc[r] == o["acc"] or abs(o["dG"] - o["thresh"]) <= DG_ABS, (kind, r)
