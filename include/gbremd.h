@@ -10,7 +10,8 @@
  *  - A batch holds M replicas (independent molecules) packed back to back;
  *    replica r owns atoms [atom_off[r], atom_off[r+1]) of every per-atom array.
  *  - Array arguments are DEVICE pointers owned by the caller unless marked
- *    "host".  The library owns only what gb_ctx_create allocates (workspace,
+ *    "host".  Per-atom arrays may be NULL when every replica of the batch is
+ *    empty (N = 0).  The library owns only what gb_ctx_create allocates (workspace,
  *    work lists, captured graphs) and frees it in gb_ctx_destroy.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *    Every call only enqueues work on that stream and returns; outputs are
@@ -310,6 +311,20 @@ typedef struct {
                                the wrap pair has its first slot at the ladder's end).  An
                                exchange skipped for a corrupt state counts as neither.
                                The caller zeroes it; gb_autotune_md leaves it as it was. */
+    int64_t* occ_count;     /* nullable, int64[n_slots][occ_stride]: state occupancy.  After
+                               every step with Monte Carlo attempts (and after that step's
+                               exchange), each site of each replica adds 1 to the entry of
+                               its current state: row = the grid slot the replica holds
+                               (the replica itself when grid is NULL or exchanges are off),
+                               column = the state's index among the replica's site states
+                               (site_state_off relative to the replica's first site).
+                               Counts / halts = the fraction of time in each state at each
+                               E / pH value (the titration data of Eq. 3 and Eq. 9).  Every
+                               replica must hold occ_stride site states (one site layout,
+                               as replica-exchange copies do); a replica that does not is
+                               skipped and GB_ERR_INVALID_ARG recorded.  The caller zeroes
+                               it. */
+    int32_t occ_stride;     /* site states per replica (the row length of occ_count) */
     int64_t rep_base;       /* global index of this batch's replica 0 in the Philox counters
                                of the MD noise and the Monte Carlo attempts (>= 0; 0 when the
                                batch is the whole ensemble).  A replica ensemble split over

@@ -77,7 +77,8 @@ class MDState(C.Structure):
                 ("kT", C.c_double), ("bond_k", C.c_float), ("bond_r0", C.c_float),
                 ("seed", C.c_uint64), ("step", C.c_uint64), ("attempt", C.c_uint64),
                 ("mc_every", C.c_int32), ("ex_every", C.c_int32), ("ex_dim", C.c_int32),
-                ("wrap", C.c_int32), ("mc_mode", C.c_int32), ("ex_count", _P), ("rep_base", C.c_int64)]
+                ("wrap", C.c_int32), ("mc_mode", C.c_int32), ("ex_count", _P), ("occ_count", _P),
+                ("occ_stride", C.c_int32), ("rep_base", C.c_int64)]
 
 
 class MDHost(C.Structure):
@@ -383,14 +384,18 @@ class Simulation:
     row p and E column e; exchanges run when n_E * n_pH == M > 1, along E
     (ex_dim 0), pH (1) or alternating (2, the default on a 2-D grid).
     Attributes xyzq, vel, force, R, state, pH, E, grid and ex_count (the
-    exchange counters of gb_md_state) are the live device tensors.  rep_base:
+    exchange counters of gb_md_state) are the live device tensors.
+    occupancy=True adds occ (int64 [M, states per replica]), the state
+    occupancy counts of gb_md_state.occ_count: per grid slot (per replica
+    without exchanges), how many Monte Carlo halts found a site in each
+    state; occupancy() turns them into fractions.  rep_base:
     global index of replica 0 in the random-number counters (a part of an
     ensemble split over processes; shard.ShardedSimulation sets it)."""
 
     def __init__(self, atom_off, xyzq, rad_screen, params: Optional[Params] = None, sites=None, pH=None,
                  E=None, E_ladder=None, pH_ladder=None, *, dt=0.002, friction=10.0, mass=12.0,
                  temperature=300.0, bond_k=300.0, bond_r0=1.5, seed=0, mc_every=10, ex_every=100,
-                 ex_dim=None, wrap=True, mc_mode=0, device=0, rep_base=0):
+                 ex_dim=None, wrap=True, mc_mode=0, device=0, rep_base=0, occupancy=False):
         import torch
         dev = torch.device("cuda", device)
         self.ctx = Context(atom_off, params, device)
@@ -430,6 +435,16 @@ class Simulation:
         st.wrap, st.mc_mode = 1 if wrap else 0, mc_mode
         st.ex_count = self.ex_count.data_ptr()
         st.rep_base = int(rep_base)
+        self.occ = None
+        if occupancy:
+            if sites is None:
+                raise ValueError("occupancy counts need site tables")
+            so, sso = np.asarray(sites["site_off"]), np.asarray(sites["site_state_off"])
+            per = np.diff(sso[so])
+            if len(set(per.tolist())) != 1:
+                raise ValueError("occupancy counts need one site layout in every replica")
+            self.occ = torch.zeros((M, int(per[0])), dtype=torch.int64, device=dev)
+            st.occ_count, st.occ_stride = self.occ.data_ptr(), int(per[0])
         self.st = st
         self.ctx.md_init(st)
 
@@ -449,8 +464,23 @@ class Simulation:
         """[M, 3] float64 (GB, Coulomb, soft repulsion) at the current coordinates."""
         return self.ctx.energy_forces(self.xyzq, self.rad, want=("E",))["E"]
 
+    def occupancy(self) -> np.ndarray:
+        """Fraction of the Monte Carlo halts so far that found each site state,
+        per grid slot: float64 [M, states per replica], columns in the order
+        of the replica's site states (site_state_off); NaN before the first
+        halt.  With one site per kind this is the reduced / protonated fraction
+        at each slot's E and pH (Eq. 3, Eq. 9)."""
+        if self.occ is None:
+            raise ValueError("the simulation was created without occupancy=True")
+        occ = self.occ.cpu().numpy().astype(np.float64)
+        so = self.sites.site_off_host
+        n_site = int(so[1] - so[0])
+        halts = occ.sum(axis=1, keepdims=True) / max(n_site, 1)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            return occ / halts
+
     # -- checkpoint / resume ------------------------------------------------------------
-    CHECKPOINT_ARRAYS = ("xyzq", "vel", "state", "grid", "pH", "E", "ex_count")
+    CHECKPOINT_ARRAYS = ("xyzq", "vel", "state", "grid", "pH", "E", "ex_count", "occ")
 
     def checkpoint(self, stream=None) -> dict:
         """Host copy of the dynamic state: coordinates and charges, velocities,
@@ -464,7 +494,8 @@ class Simulation:
         if stream is not None:
             stream.synchronize()
         torch.cuda.synchronize(self.xyzq.device)
-        ck = {k: getattr(self, k).cpu().numpy().copy() for k in self.CHECKPOINT_ARRAYS}
+        ck = {k: getattr(self, k).cpu().numpy().copy() for k in self.CHECKPOINT_ARRAYS
+              if getattr(self, k) is not None}
         ck["step"] = int(self.st.step)
         ck["attempt"] = int(self.st.attempt)
         ck["seed"] = int(self.st.seed)
@@ -477,6 +508,8 @@ class Simulation:
         import torch
         for k in self.CHECKPOINT_ARRAYS:
             dst = getattr(self, k)
+            if dst is None:
+                continue
             src = np.asarray(ck[k])
             if tuple(src.shape) != tuple(dst.shape):
                 raise ValueError(f"checkpoint {k} has shape {src.shape}, the simulation {tuple(dst.shape)}")

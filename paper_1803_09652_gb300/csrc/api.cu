@@ -549,6 +549,7 @@ extern "C" int gb_get_tiles(const gb_ctx* c, int32_t* wpb, int32_t* tpt) {
 
 static int check_inputs(gb_ctx* c, const float* xyzq, const float* rad) {
     if (!c) return fail(nullptr, GB_ERR_INVALID_ARG, "NULL context");
+    if (c->N == 0) return GB_OK;               // every replica empty: nothing is read
     if (!xyzq || !rad) return fail(c, GB_ERR_INVALID_ARG, "xyzq / rad_screen is NULL");
     if (!aligned(xyzq, 16) || !aligned(rad, 8))
         return fail(c, GB_ERR_INVALID_ARG, "xyzq must be 16-byte and rad_screen 8-byte aligned");
@@ -558,7 +559,7 @@ static int check_inputs(gb_ctx* c, const float* xyzq, const float* rad) {
 extern "C" int gb_born_radii(gb_ctx* c, const float* xyzq, const float* rad, float* R_out, void* stream) {
     int rc = check_inputs(c, xyzq, rad);
     if (rc) return rc;
-    if (!R_out) return fail(c, GB_ERR_INVALID_ARG, "R_out is NULL");
+    if (!R_out && c->N > 0) return fail(c, GB_ERR_INVALID_ARG, "R_out is NULL");
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     const gbk::PairArgs pa = pair_args(c, xyzq, rad);
@@ -750,7 +751,8 @@ gbk::MDArgs md_args(const gb_ctx* c, const gb_md_state* st) {
 
 int check_md(gb_ctx* c, const gb_md_state* st) {
     if (!c) return fail(nullptr, GB_ERR_INVALID_ARG, "NULL context");
-    if (!st || !st->xyzq || !st->vel || !st->force || !st->rad_screen)
+    if (!st) return fail(c, GB_ERR_INVALID_ARG, "MD state is NULL");
+    if (c->N > 0 && (!st->xyzq || !st->vel || !st->force || !st->rad_screen))
         return fail(c, GB_ERR_INVALID_ARG, "MD state buffer is NULL");
     if (!aligned(st->xyzq, 16) || !aligned(st->vel, 16) || !aligned(st->force, 16))
         return fail(c, GB_ERR_INVALID_ARG, "MD buffers must be 16-byte aligned");
@@ -812,6 +814,24 @@ int enqueue_mc(gb_ctx* c, gb_md_state* st, const gb_sites* sites, int64_t k, cud
     return GB_OK;
 }
 
+
+// State occupancy after a step with Monte Carlo attempts (and its exchange).
+int enqueue_occupancy(gb_ctx* c, gb_md_state* st, const gb_sites* sites, cudaStream_t s) {
+    if (!st->occ_count) return GB_OK;
+    gbk::OccArgs a{};
+    a.site_off = sites->site_off;
+    a.site_nstates = sites->site_nstates;
+    a.site_state_off = sites->site_state_off;
+    a.state = st->state;
+    a.grid = (st->grid && st->ex_every > 0) ? st->grid : nullptr;
+    a.M = c->M;
+    a.n_sites = sites->n_sites;
+    a.stride = st->occ_stride;
+    a.occ = (u64*)st->occ_count;
+    a.err = c->err;
+    GB_CHECK(c, gbk::launch_occupancy(a, s));
+    return GB_OK;
+}
 
 // Neighbour exchange on the (pH x E) grid; the attempt number is ctr[1], which
 // the second kernel advances.
@@ -904,6 +924,10 @@ int enqueue_steps(gb_ctx* c, gb_md_state* st, const gb_sites* sites, int64_t len
                 int rc = enqueue_exchange(c, st, sites, s);
                 if (rc) return rc;
             }
+            if (mc_due(t)) {
+                int rc = enqueue_occupancy(c, st, sites, s);
+                if (rc) return rc;
+            }
         }
         GB_CHECK(c, gbk::launch_advance_counters(c->ctr, (u64)len, 0, s));
         return GB_OK;
@@ -930,6 +954,10 @@ int enqueue_steps(gb_ctx* c, gb_md_state* st, const gb_sites* sites, int64_t len
         }
         if (ex_due(t)) {
             rc = enqueue_exchange(c, st, sites, s);
+            if (rc) return rc;
+        }
+        if (mc_due(t)) {
+            rc = enqueue_occupancy(c, st, sites, s);
             if (rc) return rc;
         }
         const int mode = gbk::MD_CLOSE | gbk::MD_KICK | (k + 1 < len ? gbk::MD_OPEN : 0);
@@ -972,6 +1000,7 @@ extern "C" int gb_md_segment(gb_ctx* c, gb_md_state* st, const gb_sites* sites, 
         rc = check_sites(c, sites);
         if (rc) return rc;
         if (st->mc_every > 0 && !st->state) return fail(c, GB_ERR_INVALID_ARG, "state is NULL");
+        if (st->occ_count && st->occ_stride <= 0) return fail(c, GB_ERR_INVALID_ARG, "occ_stride must be > 0");
         if (st->ex_every > 0 && st->grid &&
             (st->n_E * st->n_pH != c->M || !st->E_ladder || !st->pH_ladder || !st->E || !st->pH))
             return fail(c, GB_ERR_INVALID_ARG, "exchange grid does not match the batch");

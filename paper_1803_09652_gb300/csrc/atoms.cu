@@ -675,6 +675,30 @@ __global__ void k_grid_exchange(GridExArgs A) {
     vr[*pb] = values[b];
 }
 
+__global__ void k_occupancy(OccArgs A) {
+    pdl_enter();
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= A.n_sites) return;
+    int lo = 0, hi = A.M;                       // replica r with site_off[r] <= s < site_off[r+1]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (A.site_off[mid] <= s) lo = mid;
+        else hi = mid;
+    }
+    const int r = lo;
+    const int base = A.site_state_off[A.site_off[r]];
+    const int st = A.state[s];
+    if (A.site_state_off[A.site_off[r + 1]] - base != A.stride || st < 0 || st >= A.site_nstates[s]) {
+        atomicCAS(A.err, 0, GB_ERR_INVALID_ARG);
+        return;
+    }
+    int g = r;
+    if (A.grid)
+        for (int k = 0; k < A.M; ++k)
+            if (A.grid[k] == r) { g = k; break; }
+    atomicAdd(&A.occ[(size_t)g * A.stride + (A.site_state_off[s] - base) + st], 1ull);
+}
+
 __global__ void k_count(const int32_t* site_off, const int32_t* site_kind, const int32_t* site_nstates,
                         const int32_t* site_state_off, const int32_t* n_H, const int32_t* n_e,
                         const int32_t* state, int32_t kind, int32_t M, int32_t* out) {
@@ -735,6 +759,11 @@ cudaError_t launch_grid_exchange(const GridExArgs& a, cudaStream_t s) {
     const int n = a.n_pH * a.n_E;
     if (n < 2) return cudaSuccess;
     return launch_pdl(k_grid_exchange, dim3((n + 255) / 256), dim3(256), 0, s, a);
+}
+
+cudaError_t launch_occupancy(const OccArgs& a, cudaStream_t s) {
+    if (a.n_sites == 0) return cudaSuccess;
+    return launch_pdl(k_occupancy, dim3((a.n_sites + 127) / 128), dim3(128), 0, s, a);
 }
 
 cudaError_t launch_count(const int32_t* site_off, const int32_t* site_kind, const int32_t* site_nstates,

@@ -240,6 +240,21 @@ struct GridExArgs {
 
 cudaError_t launch_grid_exchange(const GridExArgs& a, cudaStream_t s);
 
+// State occupancy counts after a Monte Carlo halt: for every site of replica
+// r, occ[g * stride + (local index of its current state)] += 1, with g the
+// grid slot holding r (r itself without a grid).
+struct OccArgs {
+    const int32_t* site_off;
+    const int32_t* site_nstates;
+    const int32_t* site_state_off;
+    const int32_t* state;
+    const int32_t* grid;       // nullable: slot -> replica
+    int32_t M, n_sites, stride;
+    u64* occ;
+    int* err;                  // GB_ERR_INVALID_ARG: a replica's layout or a state out of range
+};
+cudaError_t launch_occupancy(const OccArgs& a, cudaStream_t s);
+
 // Persistent MD kernel (persist.cu): nsteps MD steps of the whole batch in one
 // launch, as a queue of warp items with per-(phase, replica) completion counts.
 struct PersistArgs {

@@ -101,3 +101,40 @@ def test_metrics_record_is_json_lines(pkg, tmp_path):
     assert np.array_equal(np.array(last["states"][0]), sim.state[off[0]:off[1]].cpu().numpy())
     assert sum(sum(row) for row in last["ex_attempts"]) == int(sim.ex_count[:, 0].sum())
     assert all(np.isfinite(e) for row in last["energies"] for e in row)
+
+
+@pytest.mark.parametrize("n_pH,n_E,ex_every", [(2, 2, 2), (1, 3, 0)])
+def test_occupancy_counts_match_a_host_tally(pkg, n_pH, n_E, ex_every):
+    """gb_md_state.occ_count against the states and the grid read after
+    every step: one count per site and halt, at the state's column and the
+    row of the grid slot its replica holds (the replica itself without
+    exchanges); Simulation.occupancy gives the fractions."""
+    import torch
+    device()
+    M = n_pH * n_E
+    rep = synth.make_replica(160, 71, [(1, 10, 2), (0, 8, 3), (0, 6, 2)])
+    E_lad = synth.e_ladder(n_E, half_width=0.03)
+    pH_lad = np.linspace(4.6, 5.0, n_pH)
+    b = synth.Batch([rep] * M, pH=np.repeat(pH_lad, n_E), E=np.tile(E_lad, n_pH))
+    one = synth.Batch([rep], pH=b.pH[:1], E=b.E[:1])
+    t = b.site_tables(np.tile(oracle.site_reference_energies(one, oracle_params()), M))
+    sim = pkg.Simulation(b.atom_off, b.xyzq(), b.rad_screen(), pkg.default_params(rep_k=100.0, rep_sigma=2.5),
+                         sites=t, pH=b.pH, E=b.E, E_ladder=E_lad, pH_ladder=pH_lad, mc_every=1,
+                         ex_every=ex_every or 100, seed=9, occupancy=True)
+    if not ex_every:
+        sim.st.ex_every = 0
+    S = 2 + 3 + 2
+    want = np.zeros((M, S), np.int64)
+    cols = np.array([0, 2, 5])                    # first column of each site of a replica
+    for _ in range(30):
+        sim.run(1)
+        st = sim.state.cpu().numpy().reshape(M, 3)
+        grid = sim.grid.cpu().numpy()
+        slot = np.argsort(grid) if ex_every else np.arange(M)   # replica -> slot
+        for r in range(M):
+            want[slot[r], cols + st[r]] += 1
+    sim.sync()
+    assert np.array_equal(sim.occ.cpu().numpy(), want)
+    frac = sim.occupancy()
+    assert np.allclose(frac, want / 30.0)
+    assert np.allclose(frac[:, 0] + frac[:, 1], 1.0)           # the redox site is in one of its states

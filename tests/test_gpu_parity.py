@@ -253,3 +253,26 @@ def test_exchange_grid_lines(pkg):
         pkg.eremd_exchange(torch.as_tensor(lp, device=dev), grid_g, cnt, 1, attempt, 6, KT, wrap=0,
                            n_ladders=n_E, ladder_len=n_pH, ladder_stride=1, slot_stride=n_E)
         assert np.array_equal(grid_g.cpu().numpy(), grid_o)
+
+
+def test_batch_of_empty_replicas(pkg):
+    """Every replica empty (N = 0): energies are zero, the per-atom outputs
+    empty, and an MD segment with Monte Carlo and exchanges runs to the
+    end with nothing to move."""
+    import torch
+    dev = device()
+    b = synth.random_batch([0, 0, 0], seed=10, sites=False)
+    assert b.n_atoms == 0
+    ctx = pkg.Context(b.atom_off)
+    xyzq, rad = to_dev(b, dev)
+    out = ctx.energy_forces(xyzq, rad)
+    R = ctx.born_radii(xyzq, rad)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    assert out["E"].shape == (3, 3) and bool((out["E"] == 0).all())
+    assert out["F"].numel() == 0 and R.numel() == 0
+    sim = pkg.Simulation(b.atom_off, b.xyzq(), b.rad_screen(), pkg.default_params(rep_k=100.0, rep_sigma=2.5),
+                         pH=b.pH, E=b.E)
+    sim.run(25)
+    sim.sync()
+    assert sim.step == 25
