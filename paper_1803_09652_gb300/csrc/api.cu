@@ -1113,7 +1113,7 @@ extern "C" int gb_autotune(gb_ctx* c, const float* xyzq, const float* rad, void*
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     GB_CHECK(c, cudaStreamSynchronize(s));
-    const int wpbs[] = {4, 8};
+    const int wpbs[] = {1, 2, 4, 8};
     // the cutoff kernels come with caps 1 and 3 only
     const bool cut = c->list_ctr != nullptr;
     std::vector<int> caps = cut ? std::vector<int>{1, 3} : std::vector<int>{1, 3, 4};
