@@ -1119,8 +1119,8 @@ extern "C" int gb_autotune(gb_ctx* c, const float* xyzq, const float* rad, void*
     std::vector<int> caps = cut ? std::vector<int>{1, 3} : std::vector<int>{1, 3, 4};
     std::vector<int> tpts;
     const int base = default_tpt(c);
-    for (int f : {1, 2, 4, 8, 16}) {
-        int t = std::max(1, base * f / 4);
+    for (int f : {1, 2, 4, 8, 16, 32, 64}) {
+        int t = std::max(1, base * f / 16);
         if (std::find(tpts.begin(), tpts.end(), t) == tpts.end()) tpts.push_back(t);
     }
     cudaEvent_t ev[6];

@@ -57,13 +57,15 @@ __device__ __forceinline__ double2 gb_screen(double kc, double ke_out, double ka
     return make_double2(kc - ke_out * ek, kc - ke_out * ek * (1.0 + kappa * f));
 }
 
-// Chain factor c = dE/dR * a dR/dpsi of atom g from the pair part of dE/dR
-// (cleared here) plus the self term 1/2 tF(R) q^2 / R^2.  Returns q.
+// Chain factor c = dE/dR * a dR/dpsi of atom g from the pair part of R dE/dR
+// (the pair pass sums R_i dE/dR_i; cleared here) plus the self term
+// 1/2 tF(R) q^2 / R^2.  Returns q.
 __device__ __forceinline__ double chain_factor_atom(const AtomArgs& A, int64_t g, double* R_used) {
     const double q = __ldcg(&A.xyzq[g]).w;
     const double R = __ldcg(&A.Rh[g]).x;
     const double2 t = gb_screen(A.kc, A.ke_out, A.kappa, R);
-    const double dEdR = unfix(__ldcg(&A.dR_acc[g])) + 0.5 * t.y * q * q / (R * R);
+    const double iR = 1.0 / R;
+    const double dEdR = (unfix(__ldcg(&A.dR_acc[g])) + 0.5 * t.y * q * q * iR) * iR;
     A.dR_acc[g] = 0;
     A.cc[g] = (float)(dEdR * (double)__ldcg(&A.cfac[g]));
     *R_used = R;

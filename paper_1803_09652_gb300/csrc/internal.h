@@ -26,7 +26,7 @@ struct PairArgs {
     float cut2;                // pair cutoff squared (EF_CUT kernels of the energy pass)
     float e_range2;            // energy-pass block range squared: max(cut, rep_sigma)^2
     u64* I_acc;                // [N]   Born integrals, 2^40 fixed point
-    u64* dR_acc;               // [N]   dE/dR pair part, 2^32
+    u64* dR_acc;               // [N]   R dE/dR pair part, 2^32
     u64* phi_acc;              // [N]   dE/dq pair part, 2^32
     u64* F_acc;                // [3N]  forces x | y | z, 2^32
     u64* E_acc;                // [M*4] E_GB, E_Coul, E_rep, spare, 2^32

@@ -495,17 +495,19 @@ struct Born {
 //   e_GB = -tau k_e q_i q_j / f,  f^2 = r^2 + R_i R_j exp(-D),  D = r^2 / (4 R_i R_j)
 //   e_C  =  k_c q_i q_j / r
 //   -(de/dr)/r = k_c q_i q_j / r^3 - tau k_e q_i q_j (1 - exp(-D)/4) / f^3
-//   de/dR_i = tau k_e q_i q_j exp(-D)(1 + D) R_j / (2 f^3)   (and i <-> j)
+//   R_i de/dR_i = tau k_e q_i q_j exp(-D)(R_i R_j + r^2/4) / (2 f^3)   (and i <-> j:
+//                 (1 + D) R_i R_j = R_i R_j + r^2/4, the same value on both sides)
 //   de/dq_i = (-tau k_e / f + k_c / r) q_j                  (and i <-> j)
 // Each atom carries h = sqrt(log2 e) / (2R) (negated for i), so that
 // exp(-D) = 2^(r^2 (-h_i) h_j) is two multiplies and one ex2.
 struct Energy {
-    static constexpr int NQ = 5;      // fx, fy, fz, dE/dR, dE/dq (shared memory)
+    static constexpr int NQ = 5;      // fx, fy, fz, R dE/dR, dE/dq (shared memory)
     static constexpr int UNROLL = 2;
     static constexpr int UNROLL_FAR = 2;
     static constexpr bool RADIUS_CUT = false;  // EF_CUT: the cutoff is `cut`
     struct IState {
         f2 nx, ny, nz, q, R, nh;
+        f2 qa, qk;                    // q tau k_e / 2 and q k_c (unscreened pair factors)
         long long egb, ec, er;
     };
     struct JState { float x, y, z, q, R, h, fx, fy, fz, dR, phi; };
@@ -532,6 +534,8 @@ struct Energy {
         load_one(A, base, n, i0 + 32 + lane, x1, y1, z1, q1, R1, h1);
         st.nx = make_float2(-x0, -x1); st.ny = make_float2(-y0, -y1); st.nz = make_float2(-z0, -z1);
         st.q = make_float2(q0, q1); st.R = make_float2(R0, R1); st.nh = make_float2(-h0, -h1);
+        st.qa = mul2(st.q, F2(0.5f * A.tau_ke));
+        st.qk = mul2(st.q, F2(A.kc));
         st.egb = st.ec = st.er = 0;
     }
     static __device__ __forceinline__ void load_j(const PairArgs& A, int64_t base, int n, int j, JState& st) {
@@ -550,7 +554,8 @@ struct Energy {
         const f2 qq = mul2(i.q, F2(j.q));
         const f2 nDl = mul2(r2, mul2(i.nh, F2(j.h)));                 // -D log2(e)
         const f2 e = ex22(nDl);                                       // exp(-D)
-        const f2 fsq = fma2(mul2(i.R, F2(j.R)), e, r2);
+        const f2 RR = mul2(i.R, F2(j.R));
+        const f2 fsq = fma2(RR, e, r2);
         const f2 finv = (FLAGS & EF_ENERGY) ? rsqrt2_nr(fsq) : rsqrt2(fsq);
         const f2 finv3 = mul2(mul2(finv, finv), finv);
         // solvent factors: tE in the energy (-tE q q / f), tF in its f-derivative;
@@ -564,12 +569,12 @@ struct Energy {
             const f2 tF = fma2(neg2(ekv), mul2(F2(A.kappa), f), tE);
             w = mul2(mul2(qq, F2(0.5f)), mul2(tF, finv3));           // tF q q / (2 f^3)
         } else {
-            w = mul2(mul2(qq, F2(0.5f * A.tau_ke)), finv3);
+            w = mul2(mul2(i.qa, F2(j.q)), finv3);
         }
         const f2 nu = fma2(F2(0.5f), e, F2(-2.0f));                   // -2 (1 - e/4)
-        const f2 qc = mul2(qq, F2(A.kc));
+        const f2 qc = mul2(i.qk, F2(j.q));
         f2 fr = fma2(qc, mul2(rinv2, rinv), mul2(w, nu));
-        f2 G = mul2(mul2(w, e), fma2(nDl, F2(-LN2), F2(1.0f)));        // w e (1 + D)
+        f2 G = mul2(mul2(w, e), fma2(r2, F2(0.25f), RR));              // w e (1 + D) R_i R_j
         Mask cm{true, true};          // pair within the cutoff (EF_STRADDLE blocks test it)
         if (FLAGS & EF_STRADDLE) {
             cm.x = r2.x <= A.cut2;
@@ -602,8 +607,8 @@ struct Energy {
         j.fx = fmaf(fr.y, dx.y, fmaf(fr.x, dx.x, j.fx));
         j.fy = fmaf(fr.y, dy.y, fmaf(fr.x, dy.x, j.fy));
         j.fz = fmaf(fr.y, dz.y, fmaf(fr.x, dz.x, j.fz));
-        p.dR = fma2(G, F2(j.R), p.dR);
-        j.dR = fmaf(G.y, i.R.y, fmaf(G.x, i.R.x, j.dR));
+        p.dR = add2(p.dR, G);
+        j.dR += G.x + G.y;
         if (FLAGS & EF_PHI) {
             f2 P = keep<MODE>(fma2(neg2(tE), finv, mul2(F2(A.kc), rinv)), m);
             if (FLAGS & EF_STRADDLE) P = sel2(P, cm);
