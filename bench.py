@@ -17,7 +17,7 @@ sequence per replica, no graph), the dominant pass's FP32 roofline, an
 end-to-end number through gb_md_segment_host with the state in pinned host
 memory, and the FP64 oracle on host cores.
 
---impl reference times the FP64 CPU oracle (the reference arm of this build)
+--impl reference times the FP64 CPU oracle (the reference arm)
 on the same workload.
 """
 from __future__ import annotations
