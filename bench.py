@@ -43,7 +43,7 @@ FP32_LANES = 128           # FP32 lanes per SM
 # MUFU ops counted apart), counted on the far-field arithmetic every disjoint
 # pair needs (short polynomials); pairs in near blocks cost more, so these
 # figures are a lower bound of the FP32 work done.
-FLOPS_PER_PAIR = {"born": 35.5, "energy": 46.0, "chain": 52.5}
+FLOPS_PER_PAIR = {"born": 34.0, "energy": 43.0, "chain": 51.0}
 MUFU_PER_PAIR = {"born": 1, "energy": 3, "chain": 1}
 PASS_NAMES = ["born", "energy", "chain"]
 
