@@ -53,3 +53,41 @@ def test_free_particle_maxwell(orc):
     expect = p.kT / (p.mass * AMU_A2_PS2_KCAL)
     # friction*dt = 0.1: velocities decorrelate in ~10 steps
     assert abs(vs.var() / expect - 1) < 0.05
+
+
+def test_harmonic_configurations_exact_at_a_large_step(orc):
+    """BAOAB samples the configurations of a harmonic system exactly at any
+    stable time step (Leimkuhler and Matthews, 2013): with ω dt = 1.2 the
+    position variance is still kT/κ, where orderings that put the O step
+    elsewhere (ABOBA, or velocity Verlet followed by O) give
+    kT/κ / (1 - (ω dt/2)^2), 56 % more.
+
+    System: two uncharged atoms of mass m joined by the chain bond with
+    r0 = 0, E = k r^2 = k |x1 - x0|^2.  The relative coordinate u = x1 - x0 is a
+    3-D harmonic oscillator of reduced mass m/2 and spring κ = 2k, and its O
+    step draws z1 - z0, the noise of mass m/2; so <u_x^2> = kT/(2k), ω^2 =
+    4k/m.  Uncharged atoms have no GB or Coulomb forces, and the spheres of
+    the two atoms (a = 1.41, s = 1.2 A) give no descreening NaN at any r > 0.
+    """
+    p0 = orc.default_params()
+    k = 0.05                                      # kcal/mol/A^2
+    m = p0.mass
+    omega = math.sqrt(4.0 * k * 418.4 / m)        # 1/ps (418.4: kcal/mol/A/amu -> A/ps^2)
+    dt = 1.2 / omega
+    p = orc.default_params(bond_k=k, bond_r0=0.0, rep_k=0.0, dt=dt, friction=omega)
+    off = np.array([0, 2], np.int64)
+    x = np.array([[0.0, 0.0, 0.0], [2.0, 1.0, -1.0]])
+    v = np.zeros((2, 3))
+    q, rho, scr = np.zeros(2), np.full(2, 1.5), np.full(2, 0.8)
+    F, _ = orc.forces_all(off, x, q, rho, scr, p)
+    us = []
+    for step in range(40000):
+        orc.md_step(off, x, v, q, rho, scr, F, 11, step, p)
+        if step >= 200:
+            us.append(x[1] - x[0])
+    us = np.array(us)
+    expect = p.kT / (2.0 * k)
+    ratio = (us ** 2).mean() / expect
+    # about 4e4 nearly independent samples per component: ~1 % standard error
+    assert abs(ratio - 1.0) < 0.04, ratio
+    assert np.abs(us.mean(axis=0)).max() < 0.1 * math.sqrt(expect)
