@@ -4,7 +4,9 @@ The paper runs Langevin dynamics with a 2 fs step (Sec. III.D); the splitting
 is BAOAB.  Pins: without friction the scheme is velocity Verlet and conserves
 the total energy (kinetic energy in kcal/mol from CODATA constants, not from
 the oracle's conversion factor); with friction a free particle samples the
-Maxwell distribution <v_x^2> = kT/m.
+Maxwell distribution <v_x^2> = kT/m; a harmonic pair at a large step keeps
+the exact configurational variance, which pins the order of the splitting
+(B A O A B) and not only its pieces.
 """
 import math
 
