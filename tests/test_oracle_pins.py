@@ -137,6 +137,25 @@ def test_gb_function_limits(orc):
     assert E[0] == pytest.approx(expect, rel=1e-13)
 
 
+@pytest.mark.parametrize("R1,R2", [(1.7, 2.3), (1.2, 1.2), (3.0, 1.4)])
+def test_gb_function_small_distance_expansion(orc, R1, R2):
+    """Between the two limits: expanding exp(-D) = 1 - D + D^2/2 - ... with
+    D = r^2 / (4 R1 R2) gives, by hand,
+        f^2 - R1 R2 = r^2 (1 - 1/4) + r^4 / (32 R1 R2) + O(r^6),
+    so the slope 3/4 at small r fixes the 4 in D, which both limits leave
+    free.  f is read back from the pair term of the oracle's GB energy."""
+    R = np.array([R1, R2])
+    q = np.array([0.5, 0.4])
+    e_self = -0.5 * TAU * KE * (q[0] ** 2 / R[0] + q[1] ** 2 / R[1])
+    RR = R1 * R2
+    for r in (0.02, 0.05, 0.1):
+        x = np.array([[0, 0, 0], [r, 0, 0]], dtype=float)
+        E = orc.energy_fixed_radii(x, q, R)
+        f = -TAU * KE * q[0] * q[1] / (E[0] - e_self)
+        slope = (f * f - RR) / (r * r)
+        assert slope == pytest.approx(0.75 + r * r / (32.0 * RR), abs=r ** 4 / RR ** 2 * 0.01 + 1e-9)
+
+
 def test_obc_zero_descreening_and_hct_limit(orc):
     """psi -> 0 gives R = rho - offset; with alpha=1, beta=gamma=0 and small psi
     the OBC radius reduces to the HCT radius 1/R = 1/a - I a / rho."""
